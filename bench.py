@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: Gsamples/s of the modified-ziggurat generator on GB300.
+
+A step is one pass of the hot path (layer index, fast path, fringe) over one
+batch: n = 2^28 standard normals in FP64 (2 GiB, larger than the 129 MB L2,
+so no flush is needed), each step on fresh counters.  One JSON line on
+rank 0.  `--impl reference` times the CPU oracle on the host cores instead
+(rank 0 only).  Multi-GPU: one process per GPU under torchrun, each rank on
+its own counter range (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Gsamples/s (exp & normal, FP64/FP32) and % HBM-write roofline; batched vs plain"
+UNIT = "Gsamples/s"
+DEFAULT_WORKLOAD = "normal_f64_2p28"
+KERNEL_SRC = os.path.join(ROOT, "paper_1403_6870_gb300", "csrc", "zig_gen.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gen_kernel_normal_f64_traffic.txt")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=4000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="zig", choices=["zig", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
+    p.add_argument("--n", type=int, default=None,
+                   help="override the per-step size (for small profiling captures)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the CPU baseline, e2e and variant measurements")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(n: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to n
+    samples, or None if the kernel source changed since it was taken."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_sample"]) * n
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=self.tmp, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        with open(self.tmp.name) as f:
+            rows = [r.split(",") for r in f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(dist: int, dtype: int, offset: int, n: int):
+    """Oracle throughput (samples/s) on all host cores for n counters."""
+    from oracle import oracle
+
+    oracle.build()
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    oracle.fill(dist, dtype, W.SEED, offset, n, nthreads=threads)
+    return n / (time.perf_counter() - t0), threads
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    c = W.WORKLOADS[args.workload]
+    from oracle import oracle
+
+    oracle.build()
+    threads = oracle.default_threads()
+    # size each step so the whole run takes about a minute
+    cal, _ = oracle_rate(c["dist"], c["dtype"], c["offset"], 1 << 20)
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    per = int(min(max(cal * budget, 1 << 14), 1 << 26))
+    per = 1 << int(math.log2(per))
+    for k in range(args.warmup):
+        oracle.fill(c["dist"], c["dtype"], W.SEED, c["offset"] + k * per, per, nthreads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.fill(c["dist"], c["dtype"], W.SEED, c["offset"] + (args.warmup + k) * per, per,
+                    nthreads=threads)
+    dt = time.perf_counter() - t0
+    value = per * args.steps / dt / 1e9
+    sample = f"{per} counters per step of {args.workload} (fresh counters each step)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if c["dtype"] == W.F64 else "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n_per_step": per, "seed": W.SEED},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_zig(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_1403_6870_gb300 as z
+
+    z.zig_build_tables()
+    c = W.WORKLOADS[args.workload]
+    n = args.n or c["n"]
+    tdt = torch.float64 if c["dtype"] == W.F64 else torch.float32
+    esize = 8 if c["dtype"] == W.F64 else 4
+    fn = z.zig_normal if c["dist"] == W.NORMAL else z.zig_exponential
+    out = torch.empty(n, dtype=tdt, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def counter(step):  # fresh counters per step and rank (weak scaling)
+        return c["offset"] + (step * world + rank) * n
+
+    for k in range(args.warmup):
+        fn(out, n, W.SEED, counter(k), stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(args.steps):
+            fn(out, n, W.SEED, counter(args.warmup + k), stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    status = z.zig_status_poll(stream)
+    value = n * args.steps * world / (ms / 1e3) / 1e9
+    launch_ms = ms / args.steps  # one kernel launch per step
+    peak, peak_src = measured_peak()
+    achieved = n * esize / (launch_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if c["dtype"] == W.F64 else "f32",
+        "data": "synthetic (Philox counters; seed 0x0123456789ABCDEF, fresh counters per step)",
+        "config": {"workload": args.workload, "dist": "normal" if c["dist"] else "exponential",
+                   "n_per_step_per_gpu": n, "output_bytes": n * esize,
+                   "l2": "output 2 GiB per step > 129 MB L2; no flush",
+                   "parallelism": f"counter-range shards x{world}"},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(n),
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy)",
+                     "kernel": "gen_kernel<normal,double>",
+                     "algorithmic_bytes_per_launch": n * esize},
+        "device_status": z.zig_strerror(status),
+    }
+    if not args.no_extras:
+        line["e2e"] = measure_e2e(z, fn, out, n, esize, counter, stream, args)
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["cpu_baseline"] = cpu_baseline(c)
+        line["variants"] = measure_variants(z, stream)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_e2e(z, fn, out, n, esize, counter, stream, args):
+    """Same metric through the public call with the result read back to
+    pinned host memory inside the timed region every step."""
+    import torch
+
+    host = torch.empty(n, dtype=out.dtype, pin_memory=True)
+    steps = max(3, min(20, args.steps // 100))
+    for k in range(2):
+        fn(out, n, W.SEED, counter(k), stream=stream)
+        host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        fn(out, n, W.SEED, counter(k), stream=stream)
+        host.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": n * steps / (ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": n * esize, "steps": steps,
+            "note": "inputs are (seed, offset, n) launch arguments; the result is copied to "
+                    "pinned host memory every step"}
+
+
+def cpu_baseline(c):
+    n = 1 << 25
+    rate, threads = oracle_rate(c["dist"], c["dtype"], c["offset"], n)
+    return {"value": rate / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} counters of the workload, all host cores"}
+
+
+def measure_variants(z, stream, steps: int = 100):
+    """Throughput of the other dist/dtype combinations (2^28 counters each)."""
+    import torch
+
+    res = {}
+    n = 1 << 28
+    for name, dist, dtype in (("exp_f64", W.EXP, W.F64), ("normal_f64", W.NORMAL, W.F64),
+                              ("exp_f32", W.EXP, W.F32), ("normal_f32", W.NORMAL, W.F32)):
+        tdt = torch.float64 if dtype == W.F64 else torch.float32
+        es = 8 if dtype == W.F64 else 4
+        buf = torch.empty(n, dtype=tdt, device="cuda")
+        fn = z.zig_normal if dist == W.NORMAL else z.zig_exponential
+        for k in range(5):
+            fn(buf, n, W.SEED, k * n, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            fn(buf, n, W.SEED, (k + 5) * n, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = {"gsamples_s": n / (ms / 1e3) / 1e9, "gb_s": n * es / (ms / 1e3) / 1e9,
+                     "ms_per_launch": ms}
+        del buf
+    return res
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_zig(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * zig.h -- C ABI of the GB300 (sm_103a) modified-ziggurat generator.
+ *
+ * The library turns counter-based uniform bits into standard exponential
+ * and standard normal variates with the modified ziggurat of McFarland,
+ * "A modified ziggurat algorithm for generating exponentially- and
+ * normally-distributed pseudorandom numbers" (arXiv:1403.6870):
+ *   - layers of area 1/256 lie wholly under the density P(x), so a draw
+ *     whose layer index i is below L_max returns U * X_i with no rejection
+ *     test (Sec. 2; Table 1, modified column, steps 1-2);
+ *   - the remaining draws pick an overhang j from the masses A_j with an
+ *     alias table (Table 1 step 3), sample the tail (step 4; the exponential
+ *     tail by memorylessness, the normal tail by Marsaglia-Tsang, Sec. 2),
+ *     or rejection-sample the overhang box (steps 5-8), for the exponential
+ *     with the three-region test and the reflection of Appendix C item 5.
+ *
+ * Uniform source.  Philox4x32-10 (Salmon et al., SC'11).  Output element t
+ * of a call with (seed, offset) is the variate for global counter
+ * g = offset + t: its k-th uniform block is Philox(counter = (g_lo, g_hi, 0,
+ * k), key = (seed_lo, seed_hi)), giving 64-bit words w_{2k} = r0 | r1 << 32
+ * and w_{2k+1} = r2 | r3 << 32 consumed in order.  From the first word:
+ * layer index i = bits 0-7, normal sign = bit 8, U = bits 12-63 as
+ * m * 2^-52 (FP32: bits 41-63 as m * 2^-23); an alias word gives the column
+ * from bits 0-7 and a 56-bit threshold from bits 8-63 (Appendix C items
+ * 1-2).  Every variate is therefore reproducible from (seed, g) alone, and
+ * any split of [offset, offset + n) across calls gives identical bits.
+ *
+ * Conventions for every entry point below.
+ *   - Pointers named d_* or out are DEVICE pointers owned by the caller;
+ *     h_* are host pointers.  The library never allocates on a generation
+ *     call; its own tables and status word live in static device memory
+ *     from zig_build_tables until process exit.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Generation calls are stream-ordered and return as soon as
+ *     the work is enqueued; they do not synchronise.
+ *   - Errors are returned as zig_status; nothing aborts or throws across
+ *     the ABI.  Conditions detected on the device (a fringe loop reaching
+ *     its cap) are recorded in a per-device status word read by
+ *     zig_status_poll; the affected outputs are NaN.
+ *   - Calls act on the CUDA device current on the calling thread.
+ */
+#ifndef ZIG_H
+#define ZIG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum zig_status {
+  ZIG_OK = 0,
+  ZIG_E_INVAL = 1,      /* invalid argument (null pointer, bad enum/param) */
+  ZIG_E_NOTINIT = 2,    /* zig_build_tables has not run on this device */
+  ZIG_E_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  ZIG_E_NOMEM = 4,      /* caller-provided workspace too small */
+  ZIG_E_ALIGN = 5,      /* pointer not aligned to its element size */
+  ZIG_E_RANGE = 6,      /* offset + n wraps past 2^64, or size too large */
+  ZIG_E_LOOP_LIMIT = 7, /* device: a fringe loop reached its cap */
+  ZIG_E_TABLE = 8       /* host table construction failed */
+} zig_status;
+
+typedef enum zig_dtype { ZIG_F32 = 0, ZIG_F64 = 1 } zig_dtype;
+typedef enum zig_dist { ZIG_EXP = 0, ZIG_NORMAL = 1 } zig_dist;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* zig_strerror(zig_status s);
+
+/*
+ * zig_build_tables -- build the ziggurat tables and upload them to the
+ * current device.
+ *
+ * Sec. 2: for P(x) = e^-x and the half-normal sqrt(2/pi) e^{-x^2/2}, layer
+ * k solves 1/256 = X_k (P(X_k) - P(X_{k-1})) (larger root, P(X_{-1}) = 0)
+ * until no layer of area 1/256 fits (L_max = 252 exponential, 253 normal);
+ * overhang masses A_j = int_{X_j}^{X_{j-1}} P - P(X_{j-1}) dx (j = 1..L_max,
+ * j = L_max the cap above the last layer), A_0 the tail; the alias table
+ * for j ~ A (Sec. 2, Smith 2002); the exponential chord deviation eps
+ * (Sec. 2, Appendix C item 2).  Values are computed in binary128 and
+ * rounded to binary64 and binary32 (Appendix B).
+ *
+ * Idempotent and thread-safe; the host tables are built once per process
+ * and uploaded once per device.  Synchronous (not stream-capturable).
+ * Returns ZIG_OK, ZIG_E_TABLE or ZIG_E_CUDA.
+ */
+zig_status zig_build_tables(void);
+
+/* Flat copy of one distribution's tables, as used on the device.
+ * Index conventions (Sec. 2): layer k = 0..L-1 is [0, X_k] x [f_{k-1}, f_k]
+ * with f_{-1} = 0; overhang box j = 1..L is [X_j, X_{j-1}] x [f_{j-1}, f_j]
+ * with X_L = 0 and f_L = P(0); heights are e^-x (exponential) and the
+ * unnormalised e^{-x^2/2} (normal).  dX[j] = X_{j-1} - X_j and
+ * df[j] = f_j - f_{j-1} are rounded from binary128 differences.
+ * Alias: column c = w & 255 and threshold t = w >> 8 give j = c if
+ * t < T[c] else alias[c]. */
+typedef struct zig_tables_export {
+  int32_t dist;
+  int32_t L;
+  int32_t imax;
+  int32_t reserved;
+  double X[257];
+  double f[257];
+  double dX[257];
+  double df[257];
+  double A[257];     /* probability masses (informational) */
+  double eps;        /* max_j chord deviation over box height (exp) */
+  double tau;        /* always-accept threshold on ux + uy (exp) */
+  double rinv;       /* RN64(1 / X_0) */
+  float X32[257];
+  float f32[257];
+  float dX32[257];
+  float df32[257];
+  float rinv32;      /* RN32(1 / X_0) */
+  float reserved2;
+  uint64_t T[256];
+  uint8_t alias[256];
+} zig_tables_export;
+
+/*
+ * zig_export_tables -- copy the host tables of dist into *h_out.
+ * Builds the host tables if needed (no device is touched).
+ * Returns ZIG_OK, ZIG_E_INVAL (bad dist or NULL) or ZIG_E_TABLE.
+ */
+zig_status zig_export_tables(zig_dist dist, zig_tables_export* h_out);
+
+/*
+ * zig_exponential -- n standard exponential variates, Exp(1), into out.
+ * zig_normal      -- n standard normal variates, N(0, 1), into out.
+ *
+ * Table 1 (modified column) with the readings stated above.  out is a
+ * device array of n float (ZIG_F32) or double (ZIG_F64) elements, aligned
+ * to its element size (any further alignment is handled internally);
+ * out[t] is the variate for counter offset + t.  n = 0 is a no-op.
+ * FP64: fast-path outputs are the correctly rounded U * X_i.  FP32: the
+ * same words, binary32 arithmetic and tables; accept/reject comparisons are
+ * made exactly in binary64 against a binary64 exp.
+ * Returns ZIG_OK, ZIG_E_INVAL (NULL out with n > 0, bad dtype),
+ * ZIG_E_ALIGN, ZIG_E_RANGE (offset + n > 2^64), ZIG_E_NOTINIT or
+ * ZIG_E_CUDA (launch failure).
+ */
+zig_status zig_exponential(void* out, uint64_t n, uint64_t seed,
+                           uint64_t offset, zig_dtype dtype, void* stream);
+zig_status zig_normal(void* out, uint64_t n, uint64_t seed, uint64_t offset,
+                      zig_dtype dtype, void* stream);
+
+/*
+ * zig_status_poll -- read and clear this device's status word.
+ * Synchronises stream first.  Returns ZIG_OK if no device-side condition
+ * was recorded since the last poll, ZIG_E_LOOP_LIMIT if a fringe loop hit
+ * its cap (those outputs are NaN), ZIG_E_NOTINIT or ZIG_E_CUDA.
+ */
+zig_status zig_status_poll(void* stream);
+
+/*
+ * zig_set_fringe_limits -- caps for the rare fringe loops: overhang
+ * attempts per variate (default 64) and exponential tail levels (default
+ * 16).  Reaching a cap writes NaN and records ZIG_E_LOOP_LIMIT instead of
+ * looping on (the chance per variate at the defaults is below 1e-15).
+ * Applies to launches enqueued after the call.  max_attempts >= 1,
+ * max_tail >= 0, both <= 1<<20, else ZIG_E_INVAL.
+ */
+zig_status zig_set_fringe_limits(int max_attempts, int max_tail);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZIG_H */

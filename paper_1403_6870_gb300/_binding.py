@@ -1,0 +1,154 @@
+"""Thin Python binding of libzig.so (include/zig.h), same names as the C ABI.
+
+Argument marshalling only: every step of generation runs in the library's
+CUDA kernels.  Device buffers are PyTorch CUDA tensors (or raw device
+addresses as ints); streams are torch.cuda.Stream objects, raw cudaStream_t
+ints, or None for the tensor's current stream.  A non-OK status raises
+ZigError.  The module fails to import when libzig.so has not been built:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libzig.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with paper_1403_6870_gb300.build.build() "
+        "(or __graft_entry__.build()); there is no CPU fallback")
+_lib = ctypes.CDLL(LIB_PATH)
+
+ZIG_OK, ZIG_E_INVAL, ZIG_E_NOTINIT, ZIG_E_CUDA, ZIG_E_NOMEM = 0, 1, 2, 3, 4
+ZIG_E_ALIGN, ZIG_E_RANGE, ZIG_E_LOOP_LIMIT, ZIG_E_TABLE = 5, 6, 7, 8
+ZIG_F32, ZIG_F64 = 0, 1
+ZIG_EXP, ZIG_NORMAL = 0, 1
+
+_u64 = ctypes.c_uint64
+_vp = ctypes.c_void_p
+_int = ctypes.c_int
+
+
+class ZigError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        super().__init__(f"{where}: {zig_strerror(status)} (status {status})")
+
+
+class zig_tables_export(ctypes.Structure):
+    _fields_ = [
+        ("dist", ctypes.c_int32), ("L", ctypes.c_int32), ("imax", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("X", ctypes.c_double * 257), ("f", ctypes.c_double * 257),
+        ("dX", ctypes.c_double * 257), ("df", ctypes.c_double * 257),
+        ("A", ctypes.c_double * 257),
+        ("eps", ctypes.c_double), ("tau", ctypes.c_double), ("rinv", ctypes.c_double),
+        ("X32", ctypes.c_float * 257), ("f32", ctypes.c_float * 257),
+        ("dX32", ctypes.c_float * 257), ("df32", ctypes.c_float * 257),
+        ("rinv32", ctypes.c_float), ("reserved2", ctypes.c_float),
+        ("T", ctypes.c_uint64 * 256), ("alias", ctypes.c_uint8 * 256),
+    ]
+
+
+def _sig(name, restype, argtypes):
+    fn = getattr(_lib, name)
+    fn.restype = restype
+    fn.argtypes = argtypes
+    return fn
+
+
+_strerror = _sig("zig_strerror", ctypes.c_char_p, [_int])
+_build_tables = _sig("zig_build_tables", _int, [])
+_export_tables = _sig("zig_export_tables", _int, [_int, ctypes.POINTER(zig_tables_export)])
+_exponential = _sig("zig_exponential", _int, [_vp, _u64, _u64, _u64, _int, _vp])
+_normal = _sig("zig_normal", _int, [_vp, _u64, _u64, _u64, _int, _vp])
+_status_poll = _sig("zig_status_poll", _int, [_vp])
+_set_limits = _sig("zig_set_fringe_limits", _int, [_int, _int])
+
+
+def zig_strerror(status: int) -> str:
+    return _strerror(int(status)).decode()
+
+
+def _check(st: int, where: str) -> None:
+    if st != ZIG_OK:
+        raise ZigError(st, where)
+
+
+def _stream_handle(stream, tensor=None):
+    if stream is None:
+        if tensor is not None and hasattr(tensor, "device"):
+            import torch
+
+            return torch.cuda.current_stream(tensor.device).cuda_stream
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _out_args(out, n, dtype):
+    """(device address, n, dtype code) from a tensor or a raw address."""
+    if hasattr(out, "data_ptr"):
+        import torch
+
+        if not out.is_cuda:
+            raise ValueError("out must be a CUDA tensor")
+        if not out.is_contiguous():
+            raise ValueError("out must be contiguous")
+        code = {torch.float32: ZIG_F32, torch.float64: ZIG_F64}.get(out.dtype)
+        if code is None:
+            raise ValueError("out must be float32 or float64")
+        if dtype is not None and dtype != code:
+            raise ValueError("dtype does not match the tensor")
+        if n is None:
+            n = out.numel()
+        elif n > out.numel():
+            raise ValueError("n exceeds the tensor size")
+        return out.data_ptr(), int(n), code
+    if dtype is None or n is None:
+        raise ValueError("raw addresses need explicit n and dtype")
+    return int(out), int(n), int(dtype)
+
+
+def zig_build_tables() -> None:
+    _check(_build_tables(), "zig_build_tables")
+
+
+def zig_export_tables(dist: int) -> zig_tables_export:
+    t = zig_tables_export()
+    _check(_export_tables(int(dist), ctypes.byref(t)), "zig_export_tables")
+    return t
+
+
+def zig_exponential(out, n=None, seed: int = 0, offset: int = 0, dtype=None, stream=None) -> None:
+    ptr, n, code = _out_args(out, n, dtype)
+    _check(_exponential(ptr, n, seed & (2**64 - 1), offset & (2**64 - 1), code,
+                        _stream_handle(stream, out)), "zig_exponential")
+
+
+def zig_normal(out, n=None, seed: int = 0, offset: int = 0, dtype=None, stream=None) -> None:
+    ptr, n, code = _out_args(out, n, dtype)
+    _check(_normal(ptr, n, seed & (2**64 - 1), offset & (2**64 - 1), code,
+                   _stream_handle(stream, out)), "zig_normal")
+
+
+def zig_status_poll(stream=None) -> int:
+    """Returns the device status (ZIG_OK or ZIG_E_LOOP_LIMIT) and clears it."""
+    st = _status_poll(_stream_handle(stream))
+    if st not in (ZIG_OK, ZIG_E_LOOP_LIMIT):
+        raise ZigError(st, "zig_status_poll")
+    return st
+
+
+def zig_set_fringe_limits(max_attempts: int = 64, max_tail: int = 16) -> None:
+    _check(_set_limits(int(max_attempts), int(max_tail)), "zig_set_fringe_limits")
+
+
+def raw_call(name: str, *args) -> int:
+    """Call an exported function with raw C arguments and return its status
+    (used to exercise argument checks without raising)."""
+    table = {"zig_exponential": _exponential, "zig_normal": _normal,
+             "zig_set_fringe_limits": _set_limits, "zig_status_poll": _status_poll}
+    return int(table[name](*args))

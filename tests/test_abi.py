@@ -1,0 +1,100 @@
+"""CPU-side checks of the C ABI (no kernel launches).
+
+- libzig.so loads and exports every function declared in include/zig.h;
+- the library's host tables (built independently of the oracle) agree with
+  the oracle's: L_max equal, every binary64/binary32 entry and the alias
+  table identical;
+- argument checks that return before touching the device.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def zig():
+    from paper_1403_6870_gb300 import build
+
+    build.build()
+    import paper_1403_6870_gb300 as z
+
+    return z
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(zig_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(zig):
+    lib = ctypes.CDLL(zig._binding.LIB_PATH)
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            names += _declared(h)
+    assert "zig_normal" in names and "zig_build_tables" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_covers_all_codes(zig):
+    seen = set()
+    for s in range(9):
+        msg = zig.zig_strerror(s)
+        assert msg and msg != "unknown status"
+        seen.add(msg)
+    assert len(seen) == 9
+    assert zig.zig_strerror(99) == "unknown status"
+
+
+@pytest.mark.parametrize("dist", [0, 1])
+def test_library_tables_equal_oracle_tables(zig, orc, dist):
+    t = zig.zig_export_tables(dist)
+    r = orc.tables(dist)
+    assert t.L == r.L and t.imax == 256
+    L = t.L
+    for name in ("X", "f", "dX", "df", "X32", "f32", "dX32", "df32"):
+        a = np.ctypeslib.as_array(getattr(t, name))[: L + 1]
+        b = np.ctypeslib.as_array(getattr(r, name))[: L + 1]
+        assert np.array_equal(a, b), name
+    a = np.ctypeslib.as_array(t.A)[: L + 1]
+    b = np.ctypeslib.as_array(r.A)[: L + 1]
+    assert np.allclose(a, b, rtol=1e-15, atol=0)
+    assert (t.eps, t.tau, t.rinv, t.rinv32) == (r.eps, r.tau, r.rinv, r.rinv32)
+    assert list(t.T) == list(r.T)
+    assert list(t.alias) == list(r.alias)
+
+
+def test_argument_checks(zig):
+    call = zig.raw_call
+    Z = zig
+    # NULL output with n > 0, bad dtype
+    assert call("zig_exponential", None, 10, 1, 0, Z.ZIG_F64, None) == Z.ZIG_E_INVAL
+    assert call("zig_normal", 0x1000, 10, 1, 0, 7, None) == Z.ZIG_E_INVAL
+    # n = 0 is a no-op even with a NULL pointer
+    assert call("zig_normal", None, 0, 1, 0, Z.ZIG_F32, None) == Z.ZIG_OK
+    # element alignment
+    assert call("zig_exponential", 0x1004, 10, 1, 0, Z.ZIG_F64, None) == Z.ZIG_E_ALIGN
+    assert call("zig_exponential", 0x1002, 10, 1, 0, Z.ZIG_F32, None) == Z.ZIG_E_ALIGN
+    # counter range: offset + n may reach 2^64 but not pass it
+    assert call("zig_normal", 0x1000, 2, 1, 2**64 - 1, Z.ZIG_F64, None) == Z.ZIG_E_RANGE
+    # fringe limits
+    assert call("zig_set_fringe_limits", 0, 16) == Z.ZIG_E_INVAL
+    assert call("zig_set_fringe_limits", 64, -1) == Z.ZIG_E_INVAL
+    assert call("zig_set_fringe_limits", 64, 16) == Z.ZIG_OK
+
+
+def test_no_cpu_fallback(zig):
+    """Without a usable device a valid call reports an error, never values."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st = zig.raw_call("zig_normal", 0x1000, 1 << 10, 1, 0, zig.ZIG_F64, None)
+    assert st in (zig.ZIG_E_CUDA, zig.ZIG_E_NOTINIT)

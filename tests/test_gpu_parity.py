@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the CPU oracle.
+
+Element-by-element on the same seeded counters (rule in tests/parity.py):
+sizes the oracle finishes in seconds that span many tiles and a ragged
+tail, misaligned output pointers, tiny sizes, the 2^32 and 2^64 counter
+boundaries, split invariance, the loop-limit error path, and the full
+workloads (2^28 FP64 normals, 2^30 FP32 variates) on sampled positions
+plus distribution tests of the whole device output.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from parity import check
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def zig():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    from paper_1403_6870_gb300 import build
+
+    build.build()
+    import paper_1403_6870_gb300 as z
+
+    z.zig_build_tables()
+    return z
+
+
+def _tdt(dtype):
+    return torch.float64 if dtype == W.F64 else torch.float32
+
+
+def gpu_gen(z, dist, dtype, n, seed, offset, pad=0):
+    """Generate into a view starting `pad` elements into a fresh buffer."""
+    buf = torch.full((n + pad + 8,), float("nan"), dtype=_tdt(dtype), device="cuda")
+    out = buf[pad:pad + n]
+    fn = z.zig_exponential if dist == W.EXP else z.zig_normal
+    fn(out, n, seed, offset)
+    return out, buf
+
+
+def oracle_ref(orc, dist, dtype, seed, offset, n=None, idx=None):
+    v, errs, words, margin = orc.fill(dist, dtype, seed, offset, n or 0, idx=idx,
+                                      want_words=True, want_margin=True)
+    return v, words, margin
+
+
+@pytest.mark.parametrize("name", ["exp_f64_2p20", "exp_f64_2p20_carry"])
+def test_exponential_f64_full(zig, orc, name):
+    c = W.WORKLOADS[name]
+    out, _ = gpu_gen(zig, c["dist"], c["dtype"], c["n"], W.SEED, c["offset"])
+    assert zig.zig_status_poll() == zig.ZIG_OK
+    ref, words, margin = oracle_ref(orc, c["dist"], c["dtype"], W.SEED, c["offset"], c["n"])
+    rep = check(out.cpu().numpy(), ref, words, margin)
+    assert rep["fringe"] > 10000
+
+
+@pytest.mark.parametrize("dist", [W.EXP, W.NORMAL])
+@pytest.mark.parametrize("dtype", [W.F64, W.F32])
+@pytest.mark.parametrize("pad", [0, 1, 3])
+def test_ragged_and_misaligned(zig, orc, dist, dtype, pad):
+    n = (1 << 20) + 12345
+    seed, off = 0xDEADBEEFCAFEF00D, 777
+    out, buf = gpu_gen(zig, dist, dtype, n, seed, off, pad=pad)
+    assert zig.zig_status_poll() == zig.ZIG_OK
+    ref, words, margin = oracle_ref(orc, dist, dtype, seed, off, n)
+    check(out.cpu().numpy(), ref, words, margin)
+    # nothing outside [pad, pad + n) was written
+    b = buf.cpu().numpy()
+    assert np.all(np.isnan(b[:pad])) and np.all(np.isnan(b[pad + n:]))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 31, 33, 255, 256, 257, 1023, 4097, 65537])
+def test_small_sizes(zig, orc, n):
+    for dist in (W.EXP, W.NORMAL):
+        for dtype in (W.F64, W.F32):
+            for pad in (0, 1, 2):
+                out, buf = gpu_gen(zig, dist, dtype, n, W.SEED, 5 * n, pad=pad)
+                ref, words, margin = oracle_ref(orc, dist, dtype, W.SEED, 5 * n, n)
+                check(out.cpu().numpy(), ref, words, margin)
+                b = buf.cpu().numpy()
+                assert np.all(np.isnan(b[:pad])) and np.all(np.isnan(b[pad + n:]))
+    assert zig.zig_status_poll() == zig.ZIG_OK
+
+
+def test_zero_length_is_noop(zig):
+    buf = torch.full((4,), 7.0, dtype=torch.float64, device="cuda")
+    zig.zig_normal(buf, 0, 1, 0)
+    assert torch.all(buf == 7.0)
+
+
+def test_counter_at_top_of_range(zig, orc):
+    n = 3000
+    off = 2**64 - n  # last counter is 2^64 - 1
+    for dist in (W.EXP, W.NORMAL):
+        out, _ = gpu_gen(zig, dist, W.F64, n, W.SEED, off)
+        ref, words, margin = oracle_ref(orc, dist, W.F64, W.SEED, off, n)
+        check(out.cpu().numpy(), ref, words, margin)
+    with pytest.raises(zig.ZigError):
+        gpu_gen(zig, W.EXP, W.F64, n + 1, W.SEED, off)
+
+
+def test_split_invariance(zig):
+    n, a = 1 << 20, 333331
+    for dist in (W.EXP, W.NORMAL):
+        for dtype in (W.F64, W.F32):
+            whole, _ = gpu_gen(zig, dist, dtype, n, 99, 12345)
+            part = torch.empty(n, dtype=_tdt(dtype), device="cuda")
+            fn = zig.zig_exponential if dist == W.EXP else zig.zig_normal
+            fn(part[:a], a, 99, 12345)
+            fn(part[a:], n - a, 99, 12345 + a)
+            assert torch.equal(whole.view(torch.int32 if dtype == W.F32 else torch.int64),
+                               part.view(torch.int32 if dtype == W.F32 else torch.int64))
+
+
+def test_loop_limit_reports_and_matches_oracle(zig, orc):
+    n = 1 << 20
+    try:
+        zig.zig_set_fringe_limits(1, 16)
+        orc.set_limits(1, 16)
+        out, _ = gpu_gen(zig, W.EXP, W.F64, n, W.SEED, 0)
+        assert zig.zig_status_poll() == zig.ZIG_E_LOOP_LIMIT
+        assert zig.zig_status_poll() == zig.ZIG_OK  # poll clears the word
+        v, errs, words, margin = orc.fill(W.EXP, W.F64, W.SEED, 0, n, want_words=True,
+                                          want_margin=True)
+        assert errs > 0
+        got = out.cpu().numpy()
+        assert int(np.isnan(got).sum()) == errs
+        check(got, v, words, margin)
+    finally:
+        zig.zig_set_fringe_limits(64, 16)
+        orc.set_limits(64, 16)
+
+
+def _gpu_distribution_stats(x: "torch.Tensor", dist: int):
+    """KS distance, 1024-bin equiprobable chi-square and raw moments of a
+    device array, all computed on the device in FP64."""
+    from scipy import special
+
+    n = x.numel()
+    xd = x.double()
+    q = np.arange(1, 1024) / 1024
+    edges = -np.log1p(-q) if dist == W.EXP else special.ndtri(q)
+    e = torch.tensor(edges, dtype=torch.float64, device=x.device)
+    cnt = torch.bincount(torch.bucketize(xd, e, right=True), minlength=1024).double()
+    chi2 = float(((cnt - n / 1024) ** 2 / (n / 1024)).sum())
+    s, _ = torch.sort(xd)
+    F = (1 - torch.exp(-s)) if dist == W.EXP else torch.special.ndtr(s)
+    i = torch.arange(1, n + 1, device=x.device, dtype=torch.float64)
+    D = float(torch.maximum(i / n - F, F - (i - 1) / n).max())
+    del s, F, i
+    moms = [float((xd ** k).mean()) for k in (1, 2, 3, 4)]
+    return D, chi2, moms
+
+
+def test_normal_f64_2p28_full_size(zig, orc):
+    c = W.WORKLOADS["normal_f64_2p28"]
+    n = c["n"]
+    out, _ = gpu_gen(zig, c["dist"], c["dtype"], n, W.SEED, c["offset"])
+    assert zig.zig_status_poll() == zig.ZIG_OK
+    idx = W.sample_positions(n, 1 << 20)
+    got = out[torch.from_numpy(idx.astype(np.int64)).cuda()].cpu().numpy()
+    ref, words, margin = oracle_ref(orc, c["dist"], c["dtype"], W.SEED, c["offset"], idx=idx)
+    check(got, ref, words, margin)
+    D, chi2, moms = _gpu_distribution_stats(out, W.NORMAL)
+    assert D < 1.63 / math.sqrt(n) * 1.5  # KS 1% critical value, with slack
+    assert abs(chi2 - 1023) < 6 * math.sqrt(2 * 1023)
+    for m, mu, var in zip(moms, (0, 1, 0, 3), (1, 2, 15, 96)):
+        assert abs(m - mu) < 5 * math.sqrt(var / n)
+
+
+@pytest.mark.parametrize("name", ["exp_f32_2p30", "normal_f32_2p30"])
+def test_f32_2p30_full_size(zig, orc, name):
+    c = W.WORKLOADS[name]
+    n = c["n"]
+    out, _ = gpu_gen(zig, c["dist"], c["dtype"], n, W.SEED, c["offset"])
+    assert zig.zig_status_poll() == zig.ZIG_OK
+    idx = W.sample_positions(n, 1 << 20)
+    tidx = torch.from_numpy(idx.astype(np.int64)).cuda()
+    got = out[tidx].cpu().numpy()
+    ref, words, margin = oracle_ref(orc, c["dist"], c["dtype"], W.SEED, c["offset"], idx=idx)
+    check(got, ref, words, margin)
+    # against FP64 on the same counters: |x32 - x64| and decision flips
+    r64, w64, _ = oracle_ref(orc, c["dist"], W.F64, W.SEED, c["offset"], idx=idx)
+    fast = (words == 1) & (w64 == 1)
+    d = np.abs(got[fast].astype(np.float64) - r64[fast])
+    assert d.max() <= 7.6 * 2.0**-23 + 2.0**-21
+    assert float(np.mean(words != w64)) < 1e-3
+    moms = [float((out.double() ** k).mean()) for k in (1, 2)]
+    if c["dist"] == W.EXP:
+        assert abs(moms[0] - 1) < 5 * math.sqrt(1 / n) and abs(moms[1] - 2) < 5 * math.sqrt(20 / n)
+    else:
+        assert abs(moms[0]) < 5 * math.sqrt(1 / n) and abs(moms[1] - 1) < 5 * math.sqrt(2 / n)
