@@ -33,7 +33,7 @@ def _declared(header):
 
 
 def test_exports_every_declared_symbol(zig):
-    lib = ctypes.CDLL(zig._binding.LIB_PATH)
+    lib = ctypes.CDLL(zig.LIB_PATH)
     names = []
     for h in os.listdir(os.path.join(ROOT, "include")):
         if h.endswith(".h"):
