@@ -58,7 +58,8 @@ typedef enum zig_status {
   ZIG_E_ALIGN = 5,      /* pointer not aligned to its element size */
   ZIG_E_RANGE = 6,      /* offset + n wraps past 2^64, or size too large */
   ZIG_E_LOOP_LIMIT = 7, /* device: a fringe loop reached its cap */
-  ZIG_E_TABLE = 8       /* host table construction failed */
+  ZIG_E_TABLE = 8,      /* host table construction failed */
+  ZIG_E_TIMEOUT = 9     /* device: an internal wait exceeded its limit */
 } zig_status;
 
 typedef enum zig_dtype { ZIG_F32 = 0, ZIG_F64 = 1 } zig_dtype;
@@ -148,7 +149,9 @@ zig_status zig_normal(void* out, uint64_t n, uint64_t seed, uint64_t offset,
  * zig_status_poll -- read and clear this device's status word.
  * Synchronises stream first.  Returns ZIG_OK if no device-side condition
  * was recorded since the last poll, ZIG_E_LOOP_LIMIT if a fringe loop hit
- * its cap (those outputs are NaN), ZIG_E_NOTINIT or ZIG_E_CUDA.
+ * its cap (those outputs are NaN), ZIG_E_TIMEOUT if a kernel's internal
+ * wait between its warps gave up after 20 s (its outputs are then
+ * incomplete), ZIG_E_NOTINIT or ZIG_E_CUDA.
  */
 zig_status zig_status_poll(void* stream);
 

@@ -21,7 +21,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 ZIG_OK, ZIG_E_INVAL, ZIG_E_NOTINIT, ZIG_E_CUDA, ZIG_E_NOMEM = 0, 1, 2, 3, 4
-ZIG_E_ALIGN, ZIG_E_RANGE, ZIG_E_LOOP_LIMIT, ZIG_E_TABLE = 5, 6, 7, 8
+ZIG_E_ALIGN, ZIG_E_RANGE, ZIG_E_LOOP_LIMIT, ZIG_E_TABLE, ZIG_E_TIMEOUT = 5, 6, 7, 8, 9
 ZIG_F32, ZIG_F64 = 0, 1
 ZIG_EXP, ZIG_NORMAL = 0, 1
 
@@ -137,7 +137,7 @@ def zig_normal(out, n=None, seed: int = 0, offset: int = 0, dtype=None, stream=N
 def zig_status_poll(stream=None) -> int:
     """Returns the device status (ZIG_OK or ZIG_E_LOOP_LIMIT) and clears it."""
     st = _status_poll(_stream_handle(stream))
-    if st not in (ZIG_OK, ZIG_E_LOOP_LIMIT):
+    if st not in (ZIG_OK, ZIG_E_LOOP_LIMIT, ZIG_E_TIMEOUT):
         raise ZigError(st, "zig_status_poll")
     return st
 

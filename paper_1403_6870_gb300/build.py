@@ -19,6 +19,7 @@ LIB = os.path.join(PKG, "libzig.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["zig_gen.cu"]
+CU_HEADERS = ["zig_device.cuh"]
 CPP_SOURCES = ["zig_tables.cpp"]
 
 
@@ -43,7 +44,8 @@ def _stale(obj: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(INC, "zig.h"), os.path.join(CSRC, "zig_internal.h")]
+    headers = [os.path.join(INC, "zig.h"), os.path.join(CSRC, "zig_internal.h"),
+               *[os.path.join(CSRC, h) for h in CU_HEADERS]]
     jobs = []
     objs = []
     for src in CU_SOURCES:

@@ -1,0 +1,420 @@
+// zig_device.cuh -- device-side pieces of the modified ziggurat shared by
+// every kernel of the library: the tables, Philox4x32-10, the word stream of
+// one counter and the complete sampler of Table 1 (the "general path").
+//
+// McFarland, arXiv:1403.6870, Table 1 (modified column):
+//   1. generate U_1 and i;  2. if i < L_max return U_1 X_i;
+//   3. generate j from A;   4. if j = 0 return a value from the tail;
+//   5-8. rejection-sample overhang box j.
+// Words: from the 64-bit word w, i = bits 0-7, the normal's sign = bit 8,
+// U = bits 12-63 as m 2^-52 (FP32: bits 41-63 as m 2^-23); an alias word
+// gives column c = bits 0-7 and threshold t = bits 8-63.
+#ifndef ZIG_DEVICE_CUH
+#define ZIG_DEVICE_CUH
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "zig.h"
+
+namespace zig {
+
+// ---------------------------------------------------------------------------
+// Device tables (one set per distribution; index = zig_dist)
+// ---------------------------------------------------------------------------
+struct DevTab {
+  double X[256];   // X_i; entries beyond L_max are zero (never returned)
+  double f[257];   // heights f_0..f_L (normal: unnormalised)
+  double dX[257];  // X_{j-1} - X_j
+  double df[257];  // f_j - f_{j-1}
+  float X32[256];
+  float f32[257];
+  float dX32[257];
+  float df32[257];
+  unsigned long long T[256];  // alias thresholds (56-bit scale)
+  unsigned char alias[256];
+  double tau;                  // exponential always-accept bound on ux + uy
+  unsigned long long thr52;    // smallest integer >= tau 2^52
+  unsigned int thr23;          // smallest integer >= tau 2^23
+  double rinv;                 // RN64(1 / X_0)
+  float rinv32;
+  int L;
+};
+
+// This header is included by exactly one translation unit (zig_gen.cu),
+// which owns the tables and the status word of each device.
+__device__ DevTab g_tab[2];
+__device__ unsigned int g_status;
+
+constexpr unsigned kLoopLimitBit = 1u << ZIG_E_LOOP_LIMIT;
+
+struct Limits {
+  int max_att;
+  int max_tail;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                          uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kM0 * c0;
+    const uint64_t p1 = (uint64_t)kM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+    k0 += kW0;
+    k1 += kW1;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// The ten round keys of one Philox key, (k0 + r W0, k1 + r W1).  Passed to
+// kernels by value, they live in the constant bank and enter the XORs as
+// operands instead of being recomputed per round.
+struct RoundKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+// Rounds 3..10 of Philox4x32-10 given the state after round 2, returning
+// only (r0, r1), the first word of a block.
+__device__ __forceinline__ uint2 philox_rounds3to10_first(uint32_t c0, uint32_t c1,
+                                                          uint32_t c2, uint32_t c3,
+                                                          const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kM0 * c0;
+    const uint64_t p1 = (uint64_t)kM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint2(c0, c1);
+}
+
+// Full block k of counter g (domain 0) with the round keys.
+__device__ __forceinline__ uint4 philox_block(uint64_t g, uint32_t k, const RoundKeys& rk) {
+  uint32_t c0 = (uint32_t)g, c1 = (uint32_t)(g >> 32), c2 = 0u, c3 = k;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kM0 * c0;
+    const uint64_t p1 = (uint64_t)kM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Block 0's first word of counter g (attempt 0) with the round keys.
+__device__ __forceinline__ uint2 philox_first(uint64_t g, const RoundKeys& rk) {
+  uint32_t c0 = (uint32_t)g, c1 = (uint32_t)(g >> 32), c2 = 0u, c3 = 0u;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const uint64_t p0 = (uint64_t)kM0 * c0;
+    const uint64_t p1 = (uint64_t)kM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return philox_rounds3to10_first(c0, c1, c2, c3, rk);
+}
+
+__device__ __forceinline__ uint64_t pack(uint32_t lo, uint32_t hi) {
+  return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+// Word stream of one counter g: block k = Philox((g_lo, g_hi, dom, k), key),
+// words r0 | r1 << 32 then r2 | r3 << 32.  dom = 0 is the per-index stream.
+struct Words {
+  uint32_t glo, ghi, dom, k0, k1, blk, r2, r3;
+  bool half;
+  __device__ Words(uint64_t seed, uint64_t g, uint32_t domain = 0u)
+      : glo((uint32_t)g), ghi((uint32_t)(g >> 32)), dom(domain), k0((uint32_t)seed),
+        k1((uint32_t)(seed >> 32)), blk(0), r2(0), r3(0), half(false) {}
+  __device__ uint64_t next() {
+    if (!half) {
+      const uint4 r = philox10(glo, ghi, dom, blk, k0, k1);
+      r2 = r.z;
+      r3 = r.w;
+      half = true;
+      return pack(r.x, r.y);
+    }
+    half = false;
+    ++blk;
+    return pack(r2, r3);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Precision traits: integer U, its value, table access, explicit rounding
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Prec;
+
+template <>
+struct Prec<double> {
+  typedef unsigned long long UInt;
+  static constexpr int kBits = 52;
+  static constexpr UInt kOne = 1ull << 52;
+  static __device__ __forceinline__ UInt ubits(uint64_t w) { return w >> 12; }
+  // (1 + U) from the integer: exact
+  static __device__ __forceinline__ double one_plus(UInt m) {
+    return __hiloint2double((int)(0x3FF00000u | (uint32_t)(m >> 32)), (int)(uint32_t)m);
+  }
+  static __device__ __forceinline__ double val(UInt m) { return __dsub_rn(one_plus(m), 1.0); }
+  static __device__ __forceinline__ double fmat(double a, double b, double c) {
+    return __fma_rn(a, b, c);
+  }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double X(const DevTab& t, int i) { return t.X[i]; }
+  static __device__ __forceinline__ double f(const DevTab& t, int i) { return t.f[i]; }
+  static __device__ __forceinline__ double dX(const DevTab& t, int i) { return t.dX[i]; }
+  static __device__ __forceinline__ double df(const DevTab& t, int i) { return t.df[i]; }
+  static __device__ __forceinline__ double rinv(const DevTab& t) { return t.rinv; }
+  static __device__ __forceinline__ UInt thr(const DevTab& t) { return t.thr52; }
+  static __device__ __forceinline__ double nan() {
+    return __longlong_as_double(0x7FF8000000000000ll);
+  }
+};
+
+template <>
+struct Prec<float> {
+  typedef unsigned int UInt;
+  static constexpr int kBits = 23;
+  static constexpr UInt kOne = 1u << 23;
+  static __device__ __forceinline__ UInt ubits(uint64_t w) { return (UInt)(w >> 41); }
+  static __device__ __forceinline__ float one_plus(UInt m) {
+    return __int_as_float((int)(0x3F800000u | m));
+  }
+  static __device__ __forceinline__ float val(UInt m) { return __fsub_rn(one_plus(m), 1.0f); }
+  static __device__ __forceinline__ float fmat(float a, float b, float c) {
+    return __fmaf_rn(a, b, c);
+  }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float X(const DevTab& t, int i) { return t.X32[i]; }
+  static __device__ __forceinline__ float f(const DevTab& t, int i) { return t.f32[i]; }
+  static __device__ __forceinline__ float dX(const DevTab& t, int i) { return t.dX32[i]; }
+  static __device__ __forceinline__ float df(const DevTab& t, int i) { return t.df32[i]; }
+  static __device__ __forceinline__ float rinv(const DevTab& t) { return t.rinv32; }
+  static __device__ __forceinline__ UInt thr(const DevTab& t) { return t.thr23; }
+  static __device__ __forceinline__ float nan() { return __int_as_float(0x7FC00000); }
+};
+
+// Step 3: j from the alias table.
+__device__ __forceinline__ int alias_pick(const DevTab& t, uint64_t w) {
+  const int c = (int)(w & 0xFFu);
+  return (w >> 8) < t.T[c] ? c : (int)t.alias[c];
+}
+
+// FP32 approximation of U from its integer (top 24 bits at most).
+template <typename T>
+__device__ __forceinline__ float approx_u(typename Prec<T>::UInt m) {
+  if (sizeof(T) == 8)
+    return __uint2float_rz((uint32_t)((unsigned long long)m >> 28)) * (1.0f / 16777216.0f);
+  return __uint2float_rz((uint32_t)m) * (1.0f / 8388608.0f);
+}
+
+// Exact rejection test y < exp(-a), decided first in FP32: xa, ya below are
+// FP32 approximations of x and y (from the top 24 bits of U and the binary32
+// tables) whose combined error, with that of expf, stays below 2^-17
+// relative in exp(-a) for every box of both distributions (x <= X_0).  With
+// a margin of 2^-14 the FP32 answer, when it is given, is the one the FP64
+// test y < exp(-a) would give, so the decision is always that of the FP64
+// test; only points within the margin (a fraction of about 1e-4 of the
+// attempts) evaluate the FP64 exp.
+constexpr float kPreTestMargin = 1.0f / 16384.0f;
+
+// One attempt inside overhang box j >= 1 at integer uniforms (mx, my)
+// (Table 1 steps 6-7).  Exponential: points above the chord are reflected
+// through the anti-diagonal into the lower-left triangle (Appendix C item
+// 5); below the chord by more than eps they are accepted without a test
+// (Sec. 2, three regions); the rest get the exact test y < e^-x.  Normal:
+// the exact test y < e^{-x^2/2}.  On accept x = X_j + ux (X_{j-1} - X_j).
+template <int DIST, typename T>
+__device__ __forceinline__ bool overhang_attempt(const DevTab& t, int j,
+                                                 typename Prec<T>::UInt mx,
+                                                 typename Prec<T>::UInt my, T& x) {
+  typedef Prec<T> P;
+  if (DIST == ZIG_EXP) {
+    if (mx + my > P::kOne) {
+      const typename P::UInt nx = P::kOne - my, ny = P::kOne - mx;
+      mx = nx;
+      my = ny;
+    }
+    if (mx + my < P::thr(t)) {
+      x = P::fmat(P::val(mx), P::dX(t, j), P::X(t, j));
+      return true;
+    }
+  }
+  // FP32 view of x and y for the pre-test
+  const float ux = approx_u<T>(mx), uy = approx_u<T>(my);
+  const float xa = __fmaf_rn(ux, t.dX32[j], t.X32[j]);
+  const float ya = __fmaf_rn(uy, t.df32[j], t.f32[j - 1]);
+  const float aa = DIST == ZIG_EXP ? xa : 0.5f * xa * xa;
+  const float e = expf(-aa);
+  if (ya > e * (1.0f + kPreTestMargin)) return false;
+  const T xx = P::fmat(P::val(mx), P::dX(t, j), P::X(t, j));
+  if (ya < e * (1.0f - kPreTestMargin)) {
+    x = xx;
+    return true;
+  }
+  const T y = P::fmat(P::val(my), P::df(t, j), P::f(t, j - 1));
+  const double xd = (double)xx;
+  const double a = DIST == ZIG_EXP ? xd : __dmul_rn(__dmul_rn(xd, xd), 0.5);
+  if ((double)y < exp(-a)) {
+    x = xx;
+    return true;
+  }
+  return false;
+}
+
+// Full Table 1 for the exponential from word stream w.  Step 4 uses
+// memorylessness: a tail draw is X_0 plus a fresh exponential, evaluated
+// innermost first, so depth d adds X_0 d times after the final draw.
+// Steps 5-8 keep j on rejection and draw fresh (ux, uy); the first attempt
+// reuses U_1 as ux (its bits are disjoint from i).
+template <typename T>
+__device__ T exp_general(Words& w, const DevTab& t, Limits lim, bool& err) {
+  typedef Prec<T> P;
+  int depth = 0;
+  T x;
+  for (;;) {
+    const uint64_t w0 = w.next();
+    const int i = (int)(w0 & 0xFFu);
+    const typename P::UInt m1 = P::ubits(w0);
+    if (i < t.L) {
+      x = P::mul(P::val(m1), P::X(t, i));
+      break;
+    }
+    const int j = alias_pick(t, w.next());
+    if (j == 0) {
+      if (++depth > lim.max_tail) {
+        err = true;
+        return P::nan();
+      }
+      continue;
+    }
+    typename P::UInt mx = m1;
+    for (int att = 1;; ++att) {
+      const typename P::UInt my = P::ubits(w.next());
+      if (overhang_attempt<ZIG_EXP, T>(t, j, mx, my, x)) break;
+      if (att >= lim.max_att) {
+        err = true;
+        return P::nan();
+      }
+      mx = P::ubits(w.next());
+    }
+    break;
+  }
+  for (int d = 0; d < depth; ++d) x = P::add(P::X(t, 0), x);
+  return x;
+}
+
+// Full Table 1 for the normal: sign from bit 8 of the first word; the tail
+// beyond X_0 by Marsaglia-Tsang from two exponential draws (a = E_1 / X_0,
+// accept when 2 E_2 > a^2, return X_0 + a); overhangs by rejection against
+// e^{-x^2/2}, keeping j and redrawing both uniforms.
+template <typename T>
+__device__ T normal_general(Words& w, const DevTab& te, const DevTab& tn, Limits lim,
+                            bool& err) {
+  typedef Prec<T> P;
+  const uint64_t w0 = w.next();
+  const int i = (int)(w0 & 0xFFu);
+  const bool negative = ((w0 >> 8) & 1u) != 0;
+  const typename P::UInt m1 = P::ubits(w0);
+  T x;
+  if (i < tn.L) {
+    x = P::mul(P::val(m1), P::X(tn, i));
+  } else {
+    const int j = alias_pick(tn, w.next());
+    if (j == 0) {
+      T a;
+      for (int att = 1;; ++att) {
+        a = P::mul(exp_general<T>(w, te, lim, err), P::rinv(tn));
+        const T b = exp_general<T>(w, te, lim, err);
+        if (err) return P::nan();
+        const double ad = (double)a, bd = (double)b;
+        if (__dadd_rn(bd, bd) > __dmul_rn(ad, ad)) break;
+        if (att >= lim.max_att) {
+          err = true;
+          return P::nan();
+        }
+      }
+      x = P::add(P::X(tn, 0), a);
+    } else {
+      typename P::UInt mx = m1;
+      for (int att = 1;; ++att) {
+        const typename P::UInt my = P::ubits(w.next());
+        if (overhang_attempt<ZIG_NORMAL, T>(tn, j, mx, my, x)) break;
+        if (att >= lim.max_att) {
+          err = true;
+          return P::nan();
+        }
+        mx = P::ubits(w.next());
+      }
+    }
+  }
+  return negative ? -x : x;
+}
+
+// The complete sampler for counter g of key seed.
+template <int DIST, typename T>
+__device__ __noinline__ T sample_general(uint64_t seed, uint64_t g, Limits lim) {
+  Words w(seed, g);
+  bool err = false;
+  T x = (DIST == ZIG_EXP)
+            ? exp_general<T>(w, g_tab[ZIG_EXP], lim, err)
+            : normal_general<T>(w, g_tab[ZIG_EXP], g_tab[ZIG_NORMAL], lim, err);
+  if (err) atomicOr(&g_status, kLoopLimitBit);
+  return x;
+}
+
+// ---------------------------------------------------------------------------
+// Fast path (steps 1-2) on a first word (lo, hi)
+// ---------------------------------------------------------------------------
+// x = RN(U X_i) computed as fma(1 + U, X_i, -X_i): (1 + U) X_i - X_i equals
+// U X_i exactly and the FMA rounds once.  The normal's sign (bit 8) is put
+// on the result's sign bit.
+template <int DIST>
+__device__ __forceinline__ double fast_value(uint32_t lo, uint32_t hi, const double* sX) {
+  const double X = sX[lo & 0xFFu];
+  const double one_u = __hiloint2double((int)(0x3FF00000u | (hi >> 12)),
+                                        (int)__funnelshift_r(lo, hi, 12));
+  const double x = __fma_rn(one_u, X, -X);
+  if (DIST == ZIG_EXP) return x;
+  return __hiloint2double(__double2hiint(x) ^ (int)((lo & 0x100u) << 23), __double2loint(x));
+}
+
+template <int DIST>
+__device__ __forceinline__ float fast_value(uint32_t lo, uint32_t hi, const float* sX) {
+  const float X = sX[lo & 0xFFu];
+  const float x = __fmaf_rn(__int_as_float((int)(0x3F800000u | (hi >> 9))), X, -X);
+  if (DIST == ZIG_EXP) return x;
+  return __int_as_float(__float_as_int(x) ^ (int)((lo & 0x100u) << 23));
+}
+
+}  // namespace zig
+
+#endif

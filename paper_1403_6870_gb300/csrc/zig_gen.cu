@@ -1,331 +1,39 @@
-// zig_gen.cu -- sm_103a kernels and C ABI for the modified ziggurat.
+// zig_gen.cu -- sm_103a generation kernels and the C ABI.
 //
-// McFarland, arXiv:1403.6870, Table 1 (modified column):
-//   1. generate U_1 and i;  2. if i < L_max return U_1 X_i;
-//   3. generate j from A;   4. if j = 0 return a value from the tail;
-//   5-8. rejection-sample the overhang box j.
-// Steps 1-2 are the common case (98.4% exponential, 98.8% normal).  On the
-// GPU every thread runs steps 1-2 for a fixed run of outputs with no
-// divergence: the Philox block, the word split, one shared-memory lookup of
-// X_i and one fused multiply-add, then one vector store.  A draw with
-// i >= L_max is only *recorded*: the warp ballots its fringe lanes into a
-// per-CTA shared-memory queue of output positions.  When the queue holds a
-// full CTA's worth of work (and at the end), every thread pops one position
-// and runs the whole algorithm for it from its counter (steps 1-8 with the
-// tail and overhang loops), then overwrites that output.  The fast path
-// therefore never diverges and the fringe runs with all lanes busy.
+// McFarland, arXiv:1403.6870, Table 1 (modified column).  Steps 1-2 (the
+// common case: 98.4% of exponential and 98.8% of normal draws) run for
+// every output without divergence: the Philox block, the word split, one
+// shared-memory lookup of X_i, one fused multiply-add and a vector store.
 //
-// Compiled with --fmad=false: every fused multiply-add below is written as
-// one, everything else is rounded per operation, exactly as the algorithm's
-// readings state.
+// Each CTA is warp-specialised.  Seven producer warps run only steps 1-2:
+// a draw whose layer index is not below L_max is stored like the others
+// and its position is published in a CTA shared-memory ring.  One consumer
+// warp takes positions 32 at a time and runs the rest of the algorithm for
+// them in stages, so the 32 lanes of a batch execute the same step:
+//   stage 1: steps 3-7 (alias pick, first attempt in the overhang box);
+//   stage 2: one more attempt for each rejected draw (step 8 keeps j);
+//   stage 3: tail draws, through the complete sampler of zig_device.cuh.
+// Its results overwrite the producer's placeholder values.  The producers'
+// code holds no fringe logic and no calls, so it runs without spills at the
+// register budget that four CTAs per SM allow.
+//
+// Every wait is bounded by %globaltimer; a wait that gives up records a
+// device status bit and the kernel returns.
+//
+// Compiled with --fmad=false: every fused multiply-add is written as one;
+// everything else rounds per operation, as the algorithm's readings state.
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
 
+#include "zig_device.cuh"
 #include "zig_internal.h"
 
 namespace zig {
-
-// ---------------------------------------------------------------------------
-// Device tables (one set per distribution; index = zig_dist)
-// ---------------------------------------------------------------------------
-struct DevTab {
-  double X[256];   // X_i; entries beyond L_max are zero (never returned)
-  double f[257];   // heights f_0..f_L (normal: unnormalised)
-  double dX[257];  // X_{j-1} - X_j
-  double df[257];  // f_j - f_{j-1}
-  float X32[256];
-  float f32[257];
-  float dX32[257];
-  float df32[257];
-  unsigned long long T[256];  // alias thresholds (56-bit scale)
-  unsigned char alias[256];
-  double tau;   // exponential always-accept bound on ux + uy
-  double rinv;  // RN64(1 / X_0)
-  float rinv32;
-  int L;
-};
-
-__device__ DevTab g_tab[2];
-__device__ unsigned int g_status;
-
-constexpr unsigned kLoopLimitBit = 1u << ZIG_E_LOOP_LIMIT;
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
-// ---------------------------------------------------------------------------
-constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
-constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
-
-__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2,
-                                          uint32_t c3, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint64_t p0 = (uint64_t)kM0 * c0;
-    const uint64_t p1 = (uint64_t)kM1 * c2;
-    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-    c1 = (uint32_t)p1;
-    c3 = (uint32_t)p0;
-    c0 = n0;
-    c2 = n2;
-    k0 += kW0;
-    k1 += kW1;
-  }
-  return make_uint4(c0, c1, c2, c3);
-}
-
-__device__ __forceinline__ uint64_t pack(uint32_t lo, uint32_t hi) {
-  return (uint64_t)lo | ((uint64_t)hi << 32);
-}
-
-// Word stream of one counter g: block k = Philox((g_lo, g_hi, 0, k), key);
-// words r0|r1<<32 then r2|r3<<32.
-struct Words {
-  uint32_t glo, ghi, k0, k1, blk, r2, r3;
-  bool half;
-  __device__ Words(uint64_t seed, uint64_t g)
-      : glo((uint32_t)g), ghi((uint32_t)(g >> 32)), k0((uint32_t)seed),
-        k1((uint32_t)(seed >> 32)), blk(0), r2(0), r3(0), half(false) {}
-  __device__ uint64_t next() {
-    if (!half) {
-      const uint4 r = philox10(glo, ghi, 0u, blk, k0, k1);
-      r2 = r.z;
-      r3 = r.w;
-      half = true;
-      return pack(r.x, r.y);
-    }
-    half = false;
-    ++blk;
-    return pack(r2, r3);
-  }
-};
-
-// ---------------------------------------------------------------------------
-// Precision traits: U from a word, table access, explicit FMA
-// ---------------------------------------------------------------------------
-template <typename T>
-struct Prec;
-
-template <>
-struct Prec<double> {
-  // U = (w >> 12) 2^-52, formed as (1 + U) from the bits, minus 1 (exact).
-  static __device__ __forceinline__ double one_plus_u(uint32_t lo, uint32_t hi) {
-    return __hiloint2double((int)(0x3FF00000u | (hi >> 12)),
-                            (int)__funnelshift_r(lo, hi, 12));
-  }
-  static __device__ __forceinline__ double U(uint64_t w) {
-    return __dsub_rn(one_plus_u((uint32_t)w, (uint32_t)(w >> 32)), 1.0);
-  }
-  static __device__ __forceinline__ double fmat(double a, double b, double c) {
-    return __fma_rn(a, b, c);
-  }
-  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  static __device__ __forceinline__ double X(const DevTab& t, int i) { return t.X[i]; }
-  static __device__ __forceinline__ double f(const DevTab& t, int i) { return t.f[i]; }
-  static __device__ __forceinline__ double dX(const DevTab& t, int i) { return t.dX[i]; }
-  static __device__ __forceinline__ double df(const DevTab& t, int i) { return t.df[i]; }
-  static __device__ __forceinline__ double rinv(const DevTab& t) { return t.rinv; }
-  static __device__ __forceinline__ double nan() { return __longlong_as_double(0x7FF8000000000000ll); }
-  static __device__ __forceinline__ double neg(double x) { return -x; }
-};
-
-template <>
-struct Prec<float> {
-  // U = (w >> 41) 2^-23 (top 23 bits), formed as (1 + U) minus 1.
-  static __device__ __forceinline__ float one_plus_u(uint32_t, uint32_t hi) {
-    return __int_as_float((int)(0x3F800000u | (hi >> 9)));
-  }
-  static __device__ __forceinline__ float U(uint64_t w) {
-    return __fsub_rn(one_plus_u(0u, (uint32_t)(w >> 32)), 1.0f);
-  }
-  static __device__ __forceinline__ float fmat(float a, float b, float c) {
-    return __fmaf_rn(a, b, c);
-  }
-  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float X(const DevTab& t, int i) { return t.X32[i]; }
-  static __device__ __forceinline__ float f(const DevTab& t, int i) { return t.f32[i]; }
-  static __device__ __forceinline__ float dX(const DevTab& t, int i) { return t.dX32[i]; }
-  static __device__ __forceinline__ float df(const DevTab& t, int i) { return t.df32[i]; }
-  static __device__ __forceinline__ float rinv(const DevTab& t) { return t.rinv32; }
-  static __device__ __forceinline__ float nan() { return __int_as_float(0x7FC00000); }
-  static __device__ __forceinline__ float neg(float x) { return -x; }
-};
-
-// Step 3: j from the alias table.  Column c = bits 0-7, threshold = bits
-// 8-63; j = c when the threshold is below T_c, else alias_c.
-__device__ __forceinline__ int alias_pick(const DevTab& t, uint64_t w) {
-  const int c = (int)(w & 0xFFu);
-  return (w >> 8) < t.T[c] ? c : (int)t.alias[c];
-}
-
-struct Limits {
-  int max_att;
-  int max_tail;
-};
-
-// Full Table 1 for the exponential from word stream w (the general path).
-// Step 4 uses memorylessness: a tail draw is X_0 plus a fresh exponential,
-// evaluated innermost first, so depth d adds X_0 d times after the final
-// draw.  Steps 5-8 keep j on rejection and draw fresh (ux, uy); the first
-// attempt reuses U_1 as ux (its bits are disjoint from i).
-template <typename T>
-__device__ T exp_general(Words& w, const DevTab& t, Limits lim, bool& err) {
-  typedef Prec<T> P;
-  int depth = 0;
-  T x;
-  for (;;) {
-    const uint64_t w0 = w.next();
-    const int i = (int)(w0 & 0xFFu);
-    const T U1 = P::U(w0);
-    if (i < t.L) {
-      x = P::mul(U1, P::X(t, i));
-      break;
-    }
-    const int j = alias_pick(t, w.next());
-    if (j == 0) {
-      if (++depth > lim.max_tail) {
-        err = true;
-        return P::nan();
-      }
-      continue;
-    }
-    T ux = U1;
-    for (int att = 1;; ++att) {
-      T uy = P::U(w.next());
-      // Above the chord never lies under the convex e^-x: reflect through
-      // the anti-diagonal (Appendix C item 5).
-      if (P::add(ux, uy) > (T)1) {
-        const T nx = P::add((T)1, -uy), ny = P::add((T)1, -ux);
-        ux = nx;
-        uy = ny;
-      }
-      const T xx = P::fmat(ux, P::dX(t, j), P::X(t, j));
-      // Below the chord by more than eps: under P without a test.
-      if ((double)P::add(ux, uy) < t.tau) {
-        x = xx;
-        break;
-      }
-      const T y = P::fmat(uy, P::df(t, j), P::f(t, j - 1));
-      if ((double)y < exp(-(double)xx)) {
-        x = xx;
-        break;
-      }
-      if (att >= lim.max_att) {
-        err = true;
-        return P::nan();
-      }
-      ux = P::U(w.next());
-    }
-    break;
-  }
-  for (int d = 0; d < depth; ++d) x = P::add(P::X(t, 0), x);
-  return x;
-}
-
-// Full Table 1 for the normal: sign from bit 8 of the first word; the tail
-// beyond X_0 by Marsaglia-Tsang from two exponential draws (a = E_1 / X_0,
-// accept when 2 E_2 > a^2, return X_0 + a); overhangs by plain rejection
-// y < e^{-x^2/2}, keeping j and redrawing both uniforms.
-template <typename T>
-__device__ T normal_general(Words& w, const DevTab& te, const DevTab& tn, Limits lim,
-                            bool& err) {
-  typedef Prec<T> P;
-  const uint64_t w0 = w.next();
-  const int i = (int)(w0 & 0xFFu);
-  const bool negative = ((w0 >> 8) & 1u) != 0;
-  const T U1 = P::U(w0);
-  T x;
-  if (i < tn.L) {
-    x = P::mul(U1, P::X(tn, i));
-  } else {
-    const int j = alias_pick(tn, w.next());
-    if (j == 0) {
-      T a;
-      for (int att = 1;; ++att) {
-        a = P::mul(exp_general<T>(w, te, lim, err), P::rinv(tn));
-        const T b = exp_general<T>(w, te, lim, err);
-        if (err) return P::nan();
-        const double ad = (double)a, bd = (double)b;
-        if (__dadd_rn(bd, bd) > __dmul_rn(ad, ad)) break;
-        if (att >= lim.max_att) {
-          err = true;
-          return P::nan();
-        }
-      }
-      x = P::add(P::X(tn, 0), a);
-    } else {
-      T ux = U1;
-      for (int att = 1;; ++att) {
-        const T uy = P::U(w.next());
-        const T xx = P::fmat(ux, P::dX(tn, j), P::X(tn, j));
-        const T y = P::fmat(uy, P::df(tn, j), P::f(tn, j - 1));
-        const double xd = (double)xx;
-        if ((double)y < exp(-__dmul_rn(__dmul_rn(xd, xd), 0.5))) {
-          x = xx;
-          break;
-        }
-        if (att >= lim.max_att) {
-          err = true;
-          return P::nan();
-        }
-        ux = P::U(w.next());
-      }
-    }
-  }
-  return negative ? P::neg(x) : x;
-}
-
-template <int DIST, typename T>
-__device__ __noinline__ T sample_general(uint64_t seed, uint64_t g, Limits lim) {
-  Words w(seed, g);
-  bool err = false;
-  T x = (DIST == ZIG_EXP) ? exp_general<T>(w, g_tab[ZIG_EXP], lim, err)
-                          : normal_general<T>(w, g_tab[ZIG_EXP], g_tab[ZIG_NORMAL], lim, err);
-  if (err) atomicOr(&g_status, kLoopLimitBit);
-  return x;
-}
-
-// ---------------------------------------------------------------------------
-// Fast path (steps 1-2) and vector stores
-// ---------------------------------------------------------------------------
-// x = RN(U X_i) computed as fma(1 + U, X_i, -X_i): (1 + U) X_i - X_i equals
-// U X_i exactly, and the FMA rounds once.  The normal's sign (bit 8) is
-// applied to the result's sign bit.
-template <int DIST, typename T>
-__device__ __forceinline__ T fast_value(uint32_t lo, uint32_t hi, const T* sX);
-
-template <>
-__device__ __forceinline__ double fast_value<ZIG_EXP, double>(uint32_t lo, uint32_t hi,
-                                                              const double* sX) {
-  const double X = sX[lo & 0xFFu];
-  return __fma_rn(Prec<double>::one_plus_u(lo, hi), X, -X);
-}
-template <>
-__device__ __forceinline__ double fast_value<ZIG_NORMAL, double>(uint32_t lo, uint32_t hi,
-                                                                 const double* sX) {
-  const double X = sX[lo & 0xFFu];
-  const double x = __fma_rn(Prec<double>::one_plus_u(lo, hi), X, -X);
-  return __hiloint2double(__double2hiint(x) ^ (int)((lo & 0x100u) << 23), __double2loint(x));
-}
-template <>
-__device__ __forceinline__ float fast_value<ZIG_EXP, float>(uint32_t lo, uint32_t hi,
-                                                            const float* sX) {
-  const float X = sX[lo & 0xFFu];
-  return __fmaf_rn(Prec<float>::one_plus_u(lo, hi), X, -X);
-}
-template <>
-__device__ __forceinline__ float fast_value<ZIG_NORMAL, float>(uint32_t lo, uint32_t hi,
-                                                               const float* sX) {
-  const float X = sX[lo & 0xFFu];
-  const float x = __fmaf_rn(Prec<float>::one_plus_u(lo, hi), X, -X);
-  return __int_as_float(__float_as_int(x) ^ (int)((lo & 0x100u) << 23));
-}
 
 template <typename T, int V>
 struct VecStore;
@@ -361,93 +69,423 @@ struct VecStore<float, 8> {
   }
 };
 
-constexpr int kThreads = 256;
+// Launch shape (overridable at build time for tuning sweeps).
+#ifndef ZIG_GEN_MINBLOCKS
+#define ZIG_GEN_MINBLOCKS 4
+#endif
+#ifndef ZIG_GEN_V64
+#define ZIG_GEN_V64 4
+#endif
+#ifndef ZIG_GEN_R64
+#define ZIG_GEN_R64 4
+#endif
+#ifndef ZIG_GEN_V32
+#define ZIG_GEN_V32 8
+#endif
+#ifndef ZIG_GEN_R32
+#define ZIG_GEN_R32 2
+#endif
 
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kProducerWarps = kWarps - 1;
+constexpr int kPThreads = kProducerWarps * 32;  // producer threads per CTA
+constexpr int kRing = 2048;                     // fringe ring slots per CTA
+constexpr uint64_t kEmpty = ~0ull;              // a free ring slot
+constexpr uint64_t kWholeTag = 1ull << 63;      // position needs the whole sampler
+constexpr unsigned long long kWaitLimitNs = 20ull * 1000ull * 1000ull * 1000ull;
+constexpr unsigned kWaitBit = 1u << 9;          // status bit: a wait gave up
+
+// V elements per vector store, R vector stores per producer thread per tile.
 template <typename T>
 struct GenShape;
 template <>
 struct GenShape<double> {
-  static constexpr int V = 2, R = 2;
+  static constexpr int V = ZIG_GEN_V64, R = ZIG_GEN_R64;
 };
 template <>
 struct GenShape<float> {
-  static constexpr int V = 4, R = 2;
+  static constexpr int V = ZIG_GEN_V32, R = ZIG_GEN_R32;
 };
 
-// One launch fills out[0, n): a head of < V elements up to the first
-// V-element-aligned address, nvec aligned V-vectors, then a tail.  Head and
-// tail go through the general path (queued by CTA 0).
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+  return *(const volatile unsigned*)p;
+}
+__device__ __forceinline__ uint64_t ld_volatile(const uint64_t* p) {
+  return *(const volatile uint64_t*)p;
+}
+
+// Round 1 of block 0 has counter words 2, 3 equal to zero, so its output
+// word 0 is g_hi ^ k0 and round 2's product of that word by M0 is common to
+// every counter with the same high word.  For a run of counters whose low
+// words do not wrap, round 1's products M0 g_lo are formed by adding
+// constants M0 d to one product.
+struct RunState {
+  uint64_t base;   // M0 g_lo of the run's first counter
+  uint32_t uhi;    // hi(M0 (g_hi ^ k0)) ^ k1 of round 2
+  uint32_t ulo;    // lo(M0 (g_hi ^ k0))
+  __device__ __forceinline__ RunState(uint64_t g0, const RoundKeys& rk) {
+    base = (uint64_t)kM0 * (uint32_t)g0;
+    const uint64_t u = (uint64_t)kM0 * ((uint32_t)(g0 >> 32) ^ rk.k0[0]);
+    uhi = (uint32_t)(u >> 32) ^ rk.k1[1];
+    ulo = (uint32_t)u;
+  }
+  // first word of block 0 for counter g0 + d (no wrap of the low word)
+  __device__ __forceinline__ uint2 word(uint32_t d, const RoundKeys& rk) const {
+    const uint64_t p = base + (uint64_t)kM0 * d;
+    const uint32_t n2 = (uint32_t)(p >> 32) ^ rk.k1[0], n3 = (uint32_t)p;
+    const uint64_t p1 = (uint64_t)kM1 * n2;  // round 2
+    return philox_rounds3to10_first((uint32_t)(p1 >> 32) ^ rk.k0[1], (uint32_t)p1, uhi ^ n3,
+                                    ulo, rk);
+  }
+};
+
+// Shared state of one CTA.
+template <typename T>
+struct CtaState {
+  T sX[256];
+  uint64_t ring[kRing];
+  unsigned tail;  // ring slots reserved by producers (monotone)
+  unsigned head;  // ring slots released by the consumer (monotone)
+  unsigned done;  // producer warps finished
+  // consumer's stage queues: retries (position, state, saved word), tails
+  uint64_t rp[64], rs[64], rw[64], tq[64];
+};
+
+// Producer: publish `cnt` positions per lane (pos(k), k < cnt) in the ring
+// as one warp-wide reservation.  Lane 0 reserves the warp's slots with one
+// atomic and, only if the consumer has not yet freed them, waits (bounded);
+// since a reservation never exceeds the ring, the oldest reserved slots can
+// always be written, so waits end.  A lane's own vector stores come before
+// its fence, which comes before its ring writes, so the consumer's later
+// patch of the same address is ordered after them.  Returns false if the
+// wait gave up.
+template <typename T, typename PosFn>
+__device__ __forceinline__ bool publish(CtaState<T>& sh, int cnt, PosFn pos) {
+  const int lane = threadIdx.x & 31;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  unsigned base = 0;
+  int wait = 0;
+  if (lane == 0) {
+    base = atomicAdd(&sh.tail, (unsigned)total);
+    wait = (int)(base + (unsigned)total - ld_volatile(&sh.head)) > kRing;
+  }
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  if (__shfl_sync(0xFFFFFFFFu, wait, 0)) {
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+      __nanosleep(128);
+      if (lane == 0) {
+        const bool full = (int)(base + (unsigned)total - ld_volatile(&sh.head)) > kRing;
+        wait = !full ? 0 : (globaltimer() - t0 > kWaitLimitNs ? 2 : 1);
+      }
+      wait = __shfl_sync(0xFFFFFFFFu, wait, 0);
+      if (wait == 0) break;
+      if (wait == 2) {
+        if (lane == 0) atomicOr(&g_status, kWaitBit);
+        return false;
+      }
+    }
+  }
+  __threadfence_block();
+  unsigned slot = base + (unsigned)(incl - cnt);
+  for (int k = 0; k < cnt; ++k) sh.ring[(slot++) % kRing] = pos(k);
+  return true;
+}
+
 template <int DIST, typename T>
-__global__ void __launch_bounds__(kThreads) gen_kernel(T* __restrict__ out, uint64_t n,
-                                                       uint32_t head, uint64_t nvec,
-                                                       uint64_t seed, uint64_t offset,
-                                                       Limits lim) {
+__device__ __forceinline__ void store_signed(T* out, uint64_t p, T x, bool negative) {
+  out[p] = (DIST == ZIG_NORMAL && negative) ? -x : x;
+}
+
+// Consumer queue lengths (warp-uniform), retries in the low half, tails in
+// the high half.
+struct SideCounts {
+  int retry, tail;
+};
+
+// Append one entry per lane with f set, in lane order; returns the slot.
+__device__ __forceinline__ int claim(bool f, int& n) {
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, f);
+  const int k = n + __popc(m & ((1u << (threadIdx.x & 31u)) - 1u));
+  n += __popc(m);
+  return k;
+}
+
+// Stage 1 (one fringe position per lane): steps 3-7 for the first attempt.
+// Block 0 gives U_1 (as ux) and the alias word; block 1's first word gives
+// uy.  Tail draws (j = 0) and whole-sampler items go to the tail queue;
+// rejected attempts to the retry queue with their state.
+template <int DIST, typename T>
+__device__ __forceinline__ void stage_new(T* out, uint64_t offset, const RoundKeys& rk,
+                                          Limits lim, bool active, uint64_t item,
+                                          CtaState<T>& sh, SideCounts& c) {
+  typedef Prec<T> P;
+  const DevTab& t = g_tab[DIST];
+  const bool whole = (item & kWholeTag) != 0;
+  const uint64_t p = item & ~kWholeTag;
+  const uint64_t g = offset + p;
+  const uint4 b0 = philox_block(g, 0u, rk);
+  const uint64_t w0 = pack(b0.x, b0.y);
+  const int j = alias_pick(t, pack(b0.z, b0.w));
+  const bool negative = ((w0 >> 8) & 1u) != 0;
+  const bool overhang = active && !whole && j != 0;
+  bool retry = false;
+  uint64_t state = 0, next = 0;
+  if (overhang) {
+    const uint4 b1 = philox_block(g, 1u, rk);
+    T x;
+    if (overhang_attempt<DIST, T>(t, j, P::ubits(w0), P::ubits(pack(b1.x, b1.y)), x)) {
+      store_signed<DIST, T>(out, p, x, negative);
+    } else if (1 >= lim.max_att) {
+      out[p] = P::nan();
+      atomicOr(&g_status, kLoopLimitBit);
+    } else {
+      retry = true;
+      state = (uint64_t)j | ((uint64_t)negative << 8) | (1ull << 9) | (2ull << 32);
+      next = pack(b1.z, b1.w);
+    }
+  }
+  const bool tl = active && !overhang;
+  int k = claim(tl, c.tail);
+  if (tl) sh.tq[k] = p;
+  k = claim(retry, c.retry);
+  if (retry) {
+    sh.rp[k] = p;
+    sh.rs[k] = state;
+    sh.rw[k] = next;
+  }
+}
+
+// Stage 2 (one retry per lane): ux is the saved word, uy the first word of
+// the next block, whose second word is saved for the following attempt.  j
+// is kept (Table 1 step 8 returns to step 4).  State: j in bits 0-7, the
+// normal's sign in bit 8, completed attempts in bits 9-31, next block in
+// bits 32-63.
+template <int DIST, typename T>
+__device__ __forceinline__ void stage_retry(T* out, uint64_t offset, const RoundKeys& rk,
+                                            Limits lim, bool active, uint64_t p,
+                                            uint64_t state, uint64_t word, CtaState<T>& sh,
+                                            SideCounts& c) {
+  typedef Prec<T> P;
+  const DevTab& t = g_tab[DIST];
+  const int j = (int)(state & 0xFFu);
+  const bool negative = ((state >> 8) & 1u) != 0;
+  const uint32_t att = (uint32_t)(state >> 9) & 0x7FFFFFu;
+  const uint32_t blk = (uint32_t)(state >> 32);
+  bool retry = false;
+  uint64_t nstate = 0, next = 0;
+  if (active) {
+    const uint4 b = philox_block(offset + p, blk, rk);
+    T x;
+    if (overhang_attempt<DIST, T>(t, j, P::ubits(word), P::ubits(pack(b.x, b.y)), x)) {
+      store_signed<DIST, T>(out, p, x, negative);
+    } else if ((int)(att + 1) >= lim.max_att) {
+      out[p] = P::nan();
+      atomicOr(&g_status, kLoopLimitBit);
+    } else {
+      retry = true;
+      nstate = (state & 0x1FFull) | ((uint64_t)(att + 1) << 9) | ((uint64_t)(blk + 1) << 32);
+      next = pack(b.z, b.w);
+    }
+  }
+  const int k = claim(retry, c.retry);
+  if (retry) {
+    sh.rp[k] = p;
+    sh.rs[k] = nstate;
+    sh.rw[k] = next;
+  }
+}
+
+// Consumer: run the retry and tail stages while they hold `need` or more
+// entries (at most 32 per batch).  Each side queue holds fewer than 32
+// entries before a stage-1 batch, so it stays within its 64 slots.
+template <int DIST, typename T>
+__device__ __forceinline__ void side_stages(T* out, uint64_t seed, uint64_t offset,
+                                            const RoundKeys& rk, Limits lim, int need,
+                                            CtaState<T>& sh, SideCounts& c) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    if (c.retry >= need) {
+      const int take = c.retry < 32 ? c.retry : 32;
+      const bool active = lane < take;
+      const int k = c.retry - take + lane;
+      const uint64_t p = active ? sh.rp[k] : 0, st = active ? sh.rs[k] : 0,
+                     w = active ? sh.rw[k] : 0;
+      c.retry -= take;
+      __syncwarp();  // slots read before they are refilled
+      stage_retry<DIST, T>(out, offset, rk, lim, active, p, st, w, sh, c);
+    } else if (c.tail >= need) {
+      const int take = c.tail < 32 ? c.tail : 32;
+      const bool active = lane < take;
+      const uint64_t p = active ? sh.tq[c.tail - take + lane] : 0;
+      c.tail -= take;
+      __syncwarp();
+      if (active) out[p] = sample_general<DIST, T>(seed, offset + p, lim);
+    } else {
+      break;
+    }
+    __syncwarp();
+  }
+}
+
+#ifndef ZIG_GEN_UNROLL_R
+#define ZIG_GEN_UNROLL_R 1
+#endif
+constexpr int kUnrollR = ZIG_GEN_UNROLL_R;
+
+// Steps 1-2 for one producer thread's S = V R outputs of a tile: vector r
+// holds counters g0 + r kPThreads V + [0, V) and goes to dst + r kPThreads
+// V.  Only V Philox chains are live at a time.  Returns the mask of
+// outputs (bit r V + k) whose layer index is not below L_max.  NOWRAP: the
+// low counter words do not wrap inside the run.  full: every vector lies
+// inside the output (else vector r exists only if v0 + r kPThreads < nvec).
+template <int DIST, typename T, bool NOWRAP>
+__device__ __forceinline__ unsigned producer_tile(T* __restrict__ dst, uint64_t g0, uint64_t v0,
+                                                  uint64_t nvec, bool full, const RoundKeys& rk,
+                                                  const T* sX, uint32_t L) {
   constexpr int V = GenShape<T>::V, R = GenShape<T>::R;
-  constexpr int kTile = kThreads * R;  // vectors per tile
-  constexpr int kQcap = kThreads * (V * R + 1);
-  __shared__ T sX[256];
-  __shared__ uint64_t sQ[kQcap];
-  __shared__ int sQn;
+  unsigned fm = 0;
+  const RunState run(g0, rk);
+#pragma unroll kUnrollR
+  for (int r = 0; r < R; ++r) {
+    T v[V];
+    unsigned f = 0;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const uint32_t d = (uint32_t)(r * kPThreads * V + k);
+      const uint2 w = NOWRAP ? run.word(d, rk) : philox_first(g0 + d, rk);
+      v[k] = fast_value<DIST>(w.x, w.y, sX);
+      f |= (unsigned)((w.x & 0xFFu) >= L) << k;
+    }
+    if (full || v0 + (uint64_t)(r * kPThreads) < nvec) {
+      VecStore<T, V>::st(dst + r * kPThreads * V, v);
+      fm |= f << (r * V);
+    }
+  }
+  return fm;
+}
+
+// One launch fills out[0, n): a head of < V elements up to the first
+// V-element-aligned address, nvec aligned V-vectors, then a tail of < V
+// elements; head and tail are published by CTA 0 for the whole sampler.
+// Tile t covers vectors [t kTile, (t + 1) kTile); producer thread pt stores
+// vectors t kTile + r kPThreads + pt, r < R.
+template <int DIST, typename T>
+__global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
+    gen_kernel(T* __restrict__ out, uint64_t n, uint32_t head, uint64_t nvec, uint64_t seed,
+               uint64_t offset, const RoundKeys rk, Limits lim) {
+  constexpr int V = GenShape<T>::V, R = GenShape<T>::R, S = V * R;
+  constexpr int kTile = kPThreads * R;
+  __shared__ CtaState<T> sh;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  for (int k = tid; k < 256; k += kThreads) sX[k] = Prec<T>::X(g_tab[DIST], k);
-  if (tid == 0) sQn = 0;
-  __syncthreads();
-  const uint32_t L = (uint32_t)g_tab[DIST].L;
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  const uint64_t body_end = head + nvec * V;
-  if (blockIdx.x == 0) {
-    if ((uint32_t)tid < head) sQ[atomicAdd(&sQn, 1)] = (uint64_t)tid;
-    if ((uint64_t)tid < n - body_end) sQ[atomicAdd(&sQn, 1)] = body_end + (uint64_t)tid;
+  for (int k = tid; k < 256; k += kThreads) sh.sX[k] = Prec<T>::X(g_tab[DIST], k);
+  for (int k = tid; k < kRing; k += kThreads) sh.ring[k] = kEmpty;
+  if (tid == 0) {
+    sh.tail = 0;
+    sh.head = 0;
+    sh.done = 0;
   }
-  const unsigned lt_mask = (1u << lane) - 1u;
-  T* body = out + head;
-  const uint64_t ntiles = (nvec + kTile - 1) / kTile;
+  __syncthreads();
 
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint64_t vi = tile * kTile + (uint64_t)(r * kThreads + tid);
-      const bool valid = vi < nvec;
-      T v[V];
-#pragma unroll
-      for (int k = 0; k < V; ++k) {
-        const uint64_t p = head + vi * V + (uint64_t)k;
-        const uint64_t g = offset + p;
-        // Step 1: block 0 of counter g; word 0 = r0 | r1 << 32.
-        const uint4 b = philox10((uint32_t)g, (uint32_t)(g >> 32), 0u, 0u, k0, k1);
-        // Step 2 for every lane; lanes with i >= L_max are queued.
-        v[k] = fast_value<DIST, T>(b.x, b.y, sX);
-        const bool fringe = valid && (b.x & 0xFFu) >= L;
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, fringe);
-        if (m) {
-          const int leader = __ffs(m) - 1;
-          int base = 0;
-          if (lane == leader) base = atomicAdd(&sQn, __popc(m));
-          base = __shfl_sync(0xFFFFFFFFu, base, leader);
-          if (fringe) sQ[base + __popc(m & lt_mask)] = p;
-        }
+  if (tid < kPThreads) {
+    // ---------------- producer warps: steps 1-2 only ----------------
+    const uint32_t L = (uint32_t)g_tab[DIST].L;
+    const uint64_t body_end = head + nvec * V;
+    bool ok = true;
+    if (blockIdx.x == 0 && tid < 32) {
+      // head and tail elements (fewer than V each) take the whole sampler
+      const int hc = (uint32_t)lane < head ? 1 : 0;
+      const int tc = (uint64_t)lane < n - body_end ? 1 : 0;
+      ok = publish(sh, hc + tc, [&](int k) {
+        return kWholeTag | ((k == 0 && hc) ? (uint64_t)lane : body_end + (uint64_t)lane);
+      });
+    }
+    const uint64_t ntiles = (nvec + kTile - 1) / kTile;
+    constexpr uint32_t kSpan = (uint32_t)((R - 1) * kPThreads * V + (V - 1));
+    static_assert(32 * S <= kRing, "a warp's reservation must fit the ring");
+    for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      const uint64_t v0 = tile * kTile + (uint64_t)tid;  // this thread's first vector
+      const uint64_t p0 = head + v0 * V;                   // and its first position
+      const uint64_t g0 = offset + p0;
+      T* dst = out + p0;
+      const bool full = (tile + 1) * kTile <= nvec;
+      unsigned fm;  // outputs of this thread whose layer index is >= L_max
+      if ((uint32_t)g0 <= 0xFFFFFFFFu - kSpan)
+        fm = producer_tile<DIST, T, true>(dst, g0, v0, nvec, full, rk, sh.sX, L);
+      else
+        fm = producer_tile<DIST, T, false>(dst, g0, v0, nvec, full, rk, sh.sX, L);
+      if (__any_sync(0xFFFFFFFFu, fm != 0)) {
+        const unsigned fmask = fm;
+        ok = publish(sh, __popc(fmask), [&](int k) {
+          unsigned m = fmask;
+          for (int q = 0; q < k; ++q) m &= m - 1u;  // k-th set bit
+          const int s = __ffs(m) - 1;
+          return p0 + (uint64_t)((s / V) * (kPThreads * V) + (s % V));
+        });
       }
-      if (valid) VecStore<T, V>::st(body + vi * V, v);
     }
-    __syncthreads();
-    int qn = sQn;
-    while (qn >= kThreads) {
-      const uint64_t p = sQ[qn - kThreads + tid];
-      __syncthreads();
-      if (tid == 0) sQn = qn - kThreads;
-      qn -= kThreads;
-      out[p] = sample_general<DIST, T>(seed, offset + p, lim);
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-  const int qn = sQn;
-  for (int base = 0; base < qn; base += kThreads) {
-    if (base + tid < qn) {
-      const uint64_t p = sQ[base + tid];
-      out[p] = sample_general<DIST, T>(seed, offset + p, lim);
+    __syncwarp();
+    __threadfence_block();  // every lane's ring writes before the count
+    if (lane == 0) atomicAdd(&sh.done, 1u);
+  } else {
+    // ---------------- consumer warp: steps 3-8 in stages ----------------
+    unsigned hd = 0;
+    SideCounts c{0, 0};
+    unsigned long long t0 = globaltimer();
+    for (;;) {
+      const uint64_t item = ld_volatile(&sh.ring[(hd + (unsigned)lane) % kRing]);
+      const unsigned ready = __ballot_sync(0xFFFFFFFFu, item != kEmpty);
+      const int avail = ready == 0xFFFFFFFFu ? 32 : __ffs(~ready) - 1;
+      bool last = false;
+      if (avail < 32) {
+        // lane 0 decides for the warp: done, or keep waiting, or give up
+        int state = 0;
+        if (lane == 0) {
+          if (ld_volatile(&sh.done) == (unsigned)kProducerWarps) {
+            __threadfence_block();
+            // every reserved slot is written once the producers are done
+            if (hd + (unsigned)avail == ld_volatile(&sh.tail)) state = 1;
+          }
+          if (state == 0 && globaltimer() - t0 > kWaitLimitNs) state = 2;
+        }
+        state = __shfl_sync(0xFFFFFFFFu, state, 0);
+        if (state == 2) {
+          if (lane == 0) atomicOr(&g_status, kWaitBit);
+          break;
+        }
+        if (state == 0) {
+          __nanosleep(1000);
+          continue;
+        }
+        last = true;
+      }
+      __threadfence_block();  // the producers' stores come before our patches
+      const bool active = lane < avail;
+      if (active) sh.ring[(hd + (unsigned)lane) % kRing] = kEmpty;
+      hd += (unsigned)avail;
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) *(volatile unsigned*)&sh.head = hd;
+      stage_new<DIST, T>(out, offset, rk, lim, active, active ? item : 0, sh, c);
+      __syncwarp();
+      side_stages<DIST, T>(out, seed, offset, rk, lim, last ? 1 : 32, sh, c);
+      if (last) break;
+      t0 = globaltimer();
     }
   }
 }
@@ -500,6 +538,10 @@ void to_device_layout(const zig_tables_export& h, DevTab* d) {
     d->alias[c] = h.alias[c];
   }
   d->tau = h.tau;
+  // smallest integers m with m >= tau 2^52 (2^23): ux + uy < tau holds
+  // exactly when the integer sum of the two uniforms is below them
+  d->thr52 = (unsigned long long)std::ceil(std::ldexp(h.tau, 52));
+  d->thr23 = (unsigned int)std::ceil(std::ldexp(h.tau, 23));
   d->rinv = h.rinv;
   d->rinv32 = h.rinv32;
   d->L = h.L;
@@ -512,6 +554,18 @@ zig_status current_device(int* dev) {
   }
   if (*dev < 0 || *dev >= kMaxDevices) return ZIG_E_CUDA;
   return ZIG_OK;
+}
+
+RoundKeys round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0;
+    rk.k1[r] = k1;
+    k0 += kW0;
+    k1 += kW1;
+  }
+  return rk;
 }
 
 template <int DIST, typename T>
@@ -538,13 +592,13 @@ zig_status launch_gen(void* out, uint64_t n, uint64_t seed, uint64_t offset,
   const uint64_t align_elems = (uint64_t)((V - (addr / sizeof(T)) % V) % V);
   const uint64_t head = align_elems < n ? align_elems : n;
   const uint64_t nvec = (n - head) / V;
-  const uint64_t tiles = (nvec + (uint64_t)kThreads * R - 1) / ((uint64_t)kThreads * R);
+  const uint64_t tiles = (nvec + (uint64_t)kPThreads * R - 1) / ((uint64_t)kPThreads * R);
   const uint64_t cap = (uint64_t)g_dev[dev].sms * (uint64_t)occupancy_blocks<DIST, T>(dev);
   uint64_t grid = tiles < cap ? tiles : cap;
   if (grid < 1) grid = 1;
   Limits lim{g_max_att.load(), g_max_tail.load()};
   gen_kernel<DIST, T><<<(unsigned)grid, kThreads, 0, stream>>>(
-      (T*)out, n, (uint32_t)head, nvec, seed, offset, lim);
+      (T*)out, n, (uint32_t)head, nvec, seed, offset, round_keys(seed), lim);
   if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
   return ZIG_OK;
 }
@@ -594,6 +648,7 @@ const char* zig_strerror(zig_status s) {
     case ZIG_E_RANGE: return "counter range or size out of bounds";
     case ZIG_E_LOOP_LIMIT: return "a fringe loop reached its cap (outputs are NaN)";
     case ZIG_E_TABLE: return "table construction failed";
+    case ZIG_E_TIMEOUT: return "a device-side wait exceeded its time limit";
   }
   return "unknown status";
 }
@@ -657,6 +712,7 @@ zig_status zig_status_poll(void* stream) {
     cudaGetLastError();
     return ZIG_E_CUDA;
   }
+  if (h & kWaitBit) return ZIG_E_TIMEOUT;
   if (h & kLoopLimitBit) return ZIG_E_LOOP_LIMIT;
   return ZIG_OK;
 }

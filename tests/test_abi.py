@@ -45,11 +45,11 @@ def test_exports_every_declared_symbol(zig):
 
 def test_strerror_covers_all_codes(zig):
     seen = set()
-    for s in range(9):
+    for s in range(10):
         msg = zig.zig_strerror(s)
         assert msg and msg != "unknown status"
         seen.add(msg)
-    assert len(seen) == 9
+    assert len(seen) == 10
     assert zig.zig_strerror(99) == "unknown status"
 
 
