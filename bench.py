@@ -67,18 +67,21 @@ def kernel_hash() -> str:
 
 
 def recorded_traffic(n: int):
-    """DRAM bytes per launch from the committed ncu summary, scaled to n
-    samples, or None if the kernel source changed since it was taken."""
+    """DRAM bytes (read + write) of one launch of n samples from the
+    committed ncu summary, or None if it was taken for another n or the
+    kernel source changed since."""
     try:
         kv = {}
         with open(TRAFFIC_FILE) as f:
             for line in f:
-                if ":" in line:
+                if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha256_16") != kernel_hash():
             return None
-        return float(kv["dram_bytes_per_sample"]) * n
+        if int(kv["n_captured"]) != n:
+            return None
+        return float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])
     except Exception:
         return None
 
@@ -141,6 +144,8 @@ def oracle_rate(dist: int, dtype: int, offset: int, n: int):
     from oracle import oracle
 
     oracle.build()
+    oracle.tables(oracle.EXP)
+    oracle.tables(oracle.NORMAL)  # built before the timed region
     threads = oracle.default_threads()
     t0 = time.perf_counter()
     oracle.fill(dist, dtype, W.SEED, offset, n, nthreads=threads)
