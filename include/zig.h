@@ -146,6 +146,36 @@ zig_status zig_normal(void* out, uint64_t n, uint64_t seed, uint64_t offset,
                       zig_dtype dtype, void* stream);
 
 /*
+ * zig_moments -- fused generate-and-reduce: the n variates that
+ * zig_exponential / zig_normal would write for (n, seed, offset, dtype)
+ * are generated and reduced on the device, never stored.  This is the
+ * paper's timing workload, "generating and aggregating" PRNs (Sec. 4).
+ *
+ * Outputs (device memory, overwritten):
+ *   d_sums[k] = sum of x^(k+1), k = 0..3, accumulated per thread in the
+ *     variates' precision over one tile of 16 values (FP32) or directly
+ *     (FP64) and then in FP64; the draws finished by the fringe warp are
+ *     added in their completion order, so the sums are reproducible to
+ *     about 1e-15 relative, not bit for bit;
+ *   d_hist[b], b < 4098: count of variates with floor(256 x) + 2048 = b for
+ *     -8 <= x < 8, b = 4096 for x < -8, b = 4097 for x >= 8 or NaN (exact).
+ * d_workspace: caller-owned device scratch of at least
+ *   zig_moments_workspace_bytes(dist, dtype) bytes (8-byte aligned), used
+ *   for per-block partial sums; its content need not be initialised.
+ * Enqueues two memsets (d_hist, a workspace counter) and one kernel on
+ * stream; calls on the same workspace must not overlap.
+ * Returns ZIG_OK, ZIG_E_INVAL, ZIG_E_ALIGN, ZIG_E_RANGE, ZIG_E_NOMEM
+ * (workspace too small), ZIG_E_NOTINIT or ZIG_E_CUDA.
+ */
+size_t zig_moments_workspace_bytes(zig_dist dist, zig_dtype dtype);
+/* zig_moments_workspace_bytes returns 0 if the current device has no
+ * tables yet (call zig_build_tables first). */
+zig_status zig_moments(zig_dist dist, zig_dtype dtype, uint64_t n,
+                       uint64_t seed, uint64_t offset, double* d_sums,
+                       unsigned long long* d_hist, void* d_workspace,
+                       size_t workspace_bytes, void* stream);
+
+/*
  * zig_status_poll -- read and clear this device's status word.
  * Synchronises stream first.  Returns ZIG_OK if no device-side condition
  * was recorded since the last poll, ZIG_E_LOOP_LIMIT if a fringe loop hit

@@ -64,6 +64,9 @@ _export_tables = _sig("zig_export_tables", _int, [_int, ctypes.POINTER(zig_table
 _exponential = _sig("zig_exponential", _int, [_vp, _u64, _u64, _u64, _int, _vp])
 _normal = _sig("zig_normal", _int, [_vp, _u64, _u64, _u64, _int, _vp])
 _status_poll = _sig("zig_status_poll", _int, [_vp])
+_moments_ws = _sig("zig_moments_workspace_bytes", ctypes.c_size_t, [_int, _int])
+_moments = _sig("zig_moments", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp, _vp,
+                                      ctypes.c_size_t, _vp])
 _set_limits = _sig("zig_set_fringe_limits", _int, [_int, _int])
 
 
@@ -134,6 +137,27 @@ def zig_normal(out, n=None, seed: int = 0, offset: int = 0, dtype=None, stream=N
                    _stream_handle(stream, out)), "zig_normal")
 
 
+def zig_moments_workspace_bytes(dist: int, dtype: int) -> int:
+    return int(_moments_ws(int(dist), int(dtype)))
+
+
+def zig_moments(dist: int, dtype: int, n: int, seed: int, offset: int, sums, hist, workspace,
+                stream=None) -> None:
+    """Fused generate-and-reduce into sums (4 float64) and hist (4098 int64
+    or uint64) device tensors; workspace is a device tensor of at least
+    zig_moments_workspace_bytes(dist, dtype) bytes."""
+    import torch
+
+    if sums.dtype != torch.float64 or sums.numel() < 4 or not sums.is_cuda:
+        raise ValueError("sums must be a CUDA float64 tensor of 4 elements")
+    if hist.element_size() != 8 or hist.numel() < 4098 or not hist.is_cuda:
+        raise ValueError("hist must be a CUDA 64-bit integer tensor of 4098 elements")
+    wbytes = workspace.numel() * workspace.element_size()
+    _check(_moments(int(dist), int(dtype), n, seed & (2**64 - 1), offset & (2**64 - 1),
+                    sums.data_ptr(), hist.data_ptr(), workspace.data_ptr(), wbytes,
+                    _stream_handle(stream, sums)), "zig_moments")
+
+
 def zig_status_poll(stream=None) -> int:
     """Returns the device status (ZIG_OK or ZIG_E_LOOP_LIMIT) and clears it."""
     st = _status_poll(_stream_handle(stream))
@@ -149,6 +173,6 @@ def zig_set_fringe_limits(max_attempts: int = 64, max_tail: int = 16) -> None:
 def raw_call(name: str, *args) -> int:
     """Call an exported function with raw C arguments and return its status
     (used to exercise argument checks without raising)."""
-    table = {"zig_exponential": _exponential, "zig_normal": _normal,
+    table = {"zig_exponential": _exponential, "zig_normal": _normal, "zig_moments": _moments,
              "zig_set_fringe_limits": _set_limits, "zig_status_poll": _status_poll}
     return int(table[name](*args))

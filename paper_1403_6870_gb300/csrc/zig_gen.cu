@@ -120,6 +120,9 @@ __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
 __device__ __forceinline__ uint64_t ld_volatile(const uint64_t* p) {
   return *(const volatile uint64_t*)p;
 }
+__device__ __forceinline__ double ld_volatile_d(const double* p) {
+  return *(const volatile double*)p;
+}
 
 // Round 1 of block 0 has counter words 2, 3 equal to zero, so its output
 // word 0 is g_hi ^ k0 and round 2's product of that word by M0 is common to
@@ -205,9 +208,89 @@ __device__ __forceinline__ bool publish(CtaState<T>& sh, int cnt, PosFn pos) {
   return true;
 }
 
-template <int DIST, typename T>
-__device__ __forceinline__ void store_signed(T* out, uint64_t p, T x, bool negative) {
-  out[p] = (DIST == ZIG_NORMAL && negative) ? -x : x;
+// Where values go.  A sink receives the producers' vectors (vec, with the
+// bits of the outputs still to be patched by the consumer), a per-tile
+// notification, and the consumer's final values (put).
+//
+// StoreSink: materialise into out[0, n); vector vi starts at element
+// head + vi V.
+template <typename T>
+struct StoreSink {
+  T* out;
+  uint64_t head;
+  static constexpr bool kReduce = false;
+  template <int V>
+  __device__ __forceinline__ void vec(uint64_t vi, const T* v, unsigned /*fringe*/) {
+    VecStore<T, V>::st(out + head + vi * V, v);
+  }
+  __device__ __forceinline__ void tile_end() {}
+  __device__ __forceinline__ void put(uint64_t p, T x) { out[p] = x; }
+};
+
+// Histogram bin of the fused reduction: floor(256 x) + 2048 on [-8, 8);
+// 4096 below -8; 4097 at or above 8 and for NaN.  256 x is exact in the
+// value's own precision, so the floor is exact.
+constexpr int kBins = 4098;
+__device__ __forceinline__ int hist_bin(float x) {
+  if (x < -8.0f) return 4096;
+  if (!(x < 8.0f)) return 4097;
+  return __float2int_rd(__fmul_rn(x, 256.0f)) + 2048;
+}
+__device__ __forceinline__ int hist_bin(double x) {
+  if (x < -8.0) return 4096;
+  if (!(x < 8.0)) return 4097;
+  return __double2int_rd(__dmul_rn(x, 256.0)) + 2048;
+}
+
+// MomentSink: the values are never stored; each thread accumulates x, x^2,
+// x^3, x^4 (FP32 values in FP32 over one tile, then added to FP64
+// accumulators; FP64 values in FP64) and counts the value in the CTA's
+// shared-memory histogram.  Outputs still to be patched are skipped here and
+// counted when the consumer puts their final value.
+template <typename T>
+struct MomentSink {
+  unsigned* hist;  // CTA shared histogram, kBins entries
+  double acc[4];
+  T part[4];
+  static constexpr bool kReduce = true;
+  __device__ __forceinline__ void init(unsigned* h) {
+    hist = h;
+    for (int k = 0; k < 4; ++k) {
+      acc[k] = 0.0;
+      part[k] = (T)0;
+    }
+  }
+  __device__ __forceinline__ void add(T x) {
+    typedef Prec<T> P;
+    const T x2 = P::mul(x, x);
+    part[0] = P::add(part[0], x);
+    part[1] = P::add(part[1], x2);
+    part[2] = P::fmat(x2, x, part[2]);
+    part[3] = P::fmat(x2, x2, part[3]);
+    atomicAdd(&hist[hist_bin(x)], 1u);
+  }
+  template <int V>
+  __device__ __forceinline__ void vec(uint64_t, const T* v, unsigned fringe) {
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+      if (!((fringe >> k) & 1u)) add(v[k]);
+  }
+  __device__ __forceinline__ void tile_end() {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc[k] = __dadd_rn(acc[k], (double)part[k]);
+      part[k] = (T)0;
+    }
+  }
+  __device__ __forceinline__ void put(uint64_t, T x) {
+    add(x);
+    tile_end();
+  }
+};
+
+template <int DIST, typename T, typename Sink>
+__device__ __forceinline__ void put_signed(Sink& sink, uint64_t p, T x, bool negative) {
+  sink.put(p, (DIST == ZIG_NORMAL && negative) ? -x : x);
 }
 
 // Consumer queue lengths (warp-uniform), retries in the low half, tails in
@@ -228,8 +311,8 @@ __device__ __forceinline__ int claim(bool f, int& n) {
 // Block 0 gives U_1 (as ux) and the alias word; block 1's first word gives
 // uy.  Tail draws (j = 0) and whole-sampler items go to the tail queue;
 // rejected attempts to the retry queue with their state.
-template <int DIST, typename T>
-__device__ __forceinline__ void stage_new(T* out, uint64_t offset, const RoundKeys& rk,
+template <int DIST, typename T, typename Sink>
+__device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const RoundKeys& rk,
                                           Limits lim, bool active, uint64_t item,
                                           CtaState<T>& sh, SideCounts& c) {
   typedef Prec<T> P;
@@ -248,9 +331,9 @@ __device__ __forceinline__ void stage_new(T* out, uint64_t offset, const RoundKe
     const uint4 b1 = philox_block(g, 1u, rk);
     T x;
     if (overhang_attempt<DIST, T>(t, j, P::ubits(w0), P::ubits(pack(b1.x, b1.y)), x)) {
-      store_signed<DIST, T>(out, p, x, negative);
+      put_signed<DIST, T>(sink, p, x, negative);
     } else if (1 >= lim.max_att) {
-      out[p] = P::nan();
+      sink.put(p, P::nan());
       atomicOr(&g_status, kLoopLimitBit);
     } else {
       retry = true;
@@ -274,8 +357,8 @@ __device__ __forceinline__ void stage_new(T* out, uint64_t offset, const RoundKe
 // is kept (Table 1 step 8 returns to step 4).  State: j in bits 0-7, the
 // normal's sign in bit 8, completed attempts in bits 9-31, next block in
 // bits 32-63.
-template <int DIST, typename T>
-__device__ __forceinline__ void stage_retry(T* out, uint64_t offset, const RoundKeys& rk,
+template <int DIST, typename T, typename Sink>
+__device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const RoundKeys& rk,
                                             Limits lim, bool active, uint64_t p,
                                             uint64_t state, uint64_t word, CtaState<T>& sh,
                                             SideCounts& c) {
@@ -291,9 +374,9 @@ __device__ __forceinline__ void stage_retry(T* out, uint64_t offset, const Round
     const uint4 b = philox_block(offset + p, blk, rk);
     T x;
     if (overhang_attempt<DIST, T>(t, j, P::ubits(word), P::ubits(pack(b.x, b.y)), x)) {
-      store_signed<DIST, T>(out, p, x, negative);
+      put_signed<DIST, T>(sink, p, x, negative);
     } else if ((int)(att + 1) >= lim.max_att) {
-      out[p] = P::nan();
+      sink.put(p, P::nan());
       atomicOr(&g_status, kLoopLimitBit);
     } else {
       retry = true;
@@ -312,8 +395,8 @@ __device__ __forceinline__ void stage_retry(T* out, uint64_t offset, const Round
 // Consumer: run the retry and tail stages while they hold `need` or more
 // entries (at most 32 per batch).  Each side queue holds fewer than 32
 // entries before a stage-1 batch, so it stays within its 64 slots.
-template <int DIST, typename T>
-__device__ __forceinline__ void side_stages(T* out, uint64_t seed, uint64_t offset,
+template <int DIST, typename T, typename Sink>
+__device__ __forceinline__ void side_stages(Sink& sink, uint64_t seed, uint64_t offset,
                                             const RoundKeys& rk, Limits lim, int need,
                                             CtaState<T>& sh, SideCounts& c) {
   const int lane = threadIdx.x & 31;
@@ -326,14 +409,14 @@ __device__ __forceinline__ void side_stages(T* out, uint64_t seed, uint64_t offs
                      w = active ? sh.rw[k] : 0;
       c.retry -= take;
       __syncwarp();  // slots read before they are refilled
-      stage_retry<DIST, T>(out, offset, rk, lim, active, p, st, w, sh, c);
+      stage_retry<DIST, T>(sink, offset, rk, lim, active, p, st, w, sh, c);
     } else if (c.tail >= need) {
       const int take = c.tail < 32 ? c.tail : 32;
       const bool active = lane < take;
       const uint64_t p = active ? sh.tq[c.tail - take + lane] : 0;
       c.tail -= take;
       __syncwarp();
-      if (active) out[p] = sample_general<DIST, T>(seed, offset + p, lim);
+      if (active) sink.put(p, sample_general<DIST, T>(seed, offset + p, lim));
     } else {
       break;
     }
@@ -347,13 +430,14 @@ __device__ __forceinline__ void side_stages(T* out, uint64_t seed, uint64_t offs
 constexpr int kUnrollR = ZIG_GEN_UNROLL_R;
 
 // Steps 1-2 for one producer thread's S = V R outputs of a tile: vector r
-// holds counters g0 + r kPThreads V + [0, V) and goes to dst + r kPThreads
-// V.  Only V Philox chains are live at a time.  Returns the mask of
-// outputs (bit r V + k) whose layer index is not below L_max.  NOWRAP: the
-// low counter words do not wrap inside the run.  full: every vector lies
-// inside the output (else vector r exists only if v0 + r kPThreads < nvec).
-template <int DIST, typename T, bool NOWRAP>
-__device__ __forceinline__ unsigned producer_tile(T* __restrict__ dst, uint64_t g0, uint64_t v0,
+// holds counters g0 + r kPThreads V + [0, V) and is vector v0 + r kPThreads
+// of the output.  Only V Philox chains are live at a time.  Returns the
+// mask of outputs (bit r V + k) whose layer index is not below L_max.
+// NOWRAP: the low counter words do not wrap inside the run.  full: every
+// vector lies inside the output (else vector r exists only if
+// v0 + r kPThreads < nvec).
+template <int DIST, typename T, bool NOWRAP, typename Sink>
+__device__ __forceinline__ unsigned producer_tile(Sink& sink, uint64_t g0, uint64_t v0,
                                                   uint64_t nvec, bool full, const RoundKeys& rk,
                                                   const T* sX, uint32_t L) {
   constexpr int V = GenShape<T>::V, R = GenShape<T>::R;
@@ -370,36 +454,51 @@ __device__ __forceinline__ unsigned producer_tile(T* __restrict__ dst, uint64_t 
       v[k] = fast_value<DIST>(w.x, w.y, sX);
       f |= (unsigned)((w.x & 0xFFu) >= L) << k;
     }
-    if (full || v0 + (uint64_t)(r * kPThreads) < nvec) {
-      VecStore<T, V>::st(dst + r * kPThreads * V, v);
+    const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
+    if (full || vi < nvec) {
+      sink.template vec<V>(vi, v, f);
       fm |= f << (r * V);
     }
   }
+  sink.tile_end();
   return fm;
 }
 
-// One launch fills out[0, n): a head of < V elements up to the first
+// Where the fused reduction's partial results go: per-CTA FP64 partials
+// in a caller workspace, the last CTA to finish sums them in CTA order.
+struct ReduceOut {
+  double* sums;                   // device, 4 values (output)
+  unsigned long long* hist;       // device, kBins counts (output, zeroed before launch)
+  double* part;                   // workspace: gridDim.x x 4 partial sums
+  unsigned* ticket;               // workspace: CTAs finished (zero before launch)
+};
+
+// One launch covers outputs [0, n): a head of < V elements up to the first
 // V-element-aligned address, nvec aligned V-vectors, then a tail of < V
 // elements; head and tail are published by CTA 0 for the whole sampler.
-// Tile t covers vectors [t kTile, (t + 1) kTile); producer thread pt stores
+// Tile t covers vectors [t kTile, (t + 1) kTile); producer thread pt makes
 // vectors t kTile + r kPThreads + pt, r < R.
-template <int DIST, typename T>
+template <int DIST, typename T, typename Sink>
 __global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
-    gen_kernel(T* __restrict__ out, uint64_t n, uint32_t head, uint64_t nvec, uint64_t seed,
-               uint64_t offset, const RoundKeys rk, Limits lim) {
+    gen_kernel(Sink sink, uint64_t n, uint32_t head, uint64_t nvec, uint64_t seed,
+               uint64_t offset, const RoundKeys rk, Limits lim, ReduceOut red) {
   constexpr int V = GenShape<T>::V, R = GenShape<T>::R, S = V * R;
   constexpr int kTile = kPThreads * R;
   __shared__ CtaState<T> sh;
+  __shared__ unsigned shist[Sink::kReduce ? kBins : 1];
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   for (int k = tid; k < 256; k += kThreads) sh.sX[k] = Prec<T>::X(g_tab[DIST], k);
   for (int k = tid; k < kRing; k += kThreads) sh.ring[k] = kEmpty;
+  if (Sink::kReduce)
+    for (int k = tid; k < kBins; k += kThreads) shist[k] = 0u;
   if (tid == 0) {
     sh.tail = 0;
     sh.head = 0;
     sh.done = 0;
   }
+  if constexpr (Sink::kReduce) sink.init(shist);
   __syncthreads();
 
   if (tid < kPThreads) {
@@ -422,13 +521,12 @@ __global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
       const uint64_t v0 = tile * kTile + (uint64_t)tid;  // this thread's first vector
       const uint64_t p0 = head + v0 * V;                   // and its first position
       const uint64_t g0 = offset + p0;
-      T* dst = out + p0;
       const bool full = (tile + 1) * kTile <= nvec;
       unsigned fm;  // outputs of this thread whose layer index is >= L_max
       if ((uint32_t)g0 <= 0xFFFFFFFFu - kSpan)
-        fm = producer_tile<DIST, T, true>(dst, g0, v0, nvec, full, rk, sh.sX, L);
+        fm = producer_tile<DIST, T, true>(sink, g0, v0, nvec, full, rk, sh.sX, L);
       else
-        fm = producer_tile<DIST, T, false>(dst, g0, v0, nvec, full, rk, sh.sX, L);
+        fm = producer_tile<DIST, T, false>(sink, g0, v0, nvec, full, rk, sh.sX, L);
       if (__any_sync(0xFFFFFFFFu, fm != 0)) {
         const unsigned fmask = fm;
         ok = publish(sh, __popc(fmask), [&](int k) {
@@ -481,11 +579,42 @@ __global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
       __threadfence_block();
       __syncwarp();
       if (lane == 0) *(volatile unsigned*)&sh.head = hd;
-      stage_new<DIST, T>(out, offset, rk, lim, active, active ? item : 0, sh, c);
+      stage_new<DIST, T>(sink, offset, rk, lim, active, active ? item : 0, sh, c);
       __syncwarp();
-      side_stages<DIST, T>(out, seed, offset, rk, lim, last ? 1 : 32, sh, c);
+      side_stages<DIST, T>(sink, seed, offset, rk, lim, last ? 1 : 32, sh, c);
       if (last) break;
       t0 = globaltimer();
+    }
+  }
+
+  if constexpr (Sink::kReduce) {
+    // CTA partials in thread order, then the CTA's histogram into the
+    // output; the last CTA to finish sums the partials in CTA order.
+    __shared__ double rsum[kThreads][4];
+    __shared__ bool last_cta;
+    for (int k = 0; k < 4; ++k) rsum[tid][k] = sink.acc[k];
+    __syncthreads();
+    if (tid < 4) {
+      double a = 0.0;
+      for (int t = 0; t < kThreads; ++t) a = __dadd_rn(a, rsum[t][tid]);
+      rsum[0][tid] = a;
+    }
+    for (int k = tid; k < kBins; k += kThreads)
+      if (shist[k]) atomicAdd(&red.hist[k], (unsigned long long)shist[k]);
+    __syncthreads();
+    if (tid < 4) red.part[(size_t)blockIdx.x * 4 + tid] = rsum[0][tid];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last_cta = atomicAdd(red.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last_cta) {
+      __threadfence();
+      if (tid < 4) {
+        double a = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) a = __dadd_rn(a, ld_volatile_d(&red.part[(size_t)b * 4 + tid]));
+        red.sums[tid] = a;
+      }
+      if (tid == 0) *red.ticket = 0u;
     }
   }
 }
@@ -568,14 +697,14 @@ RoundKeys round_keys(uint64_t seed) {
   return rk;
 }
 
-template <int DIST, typename T>
+template <int DIST, typename T, typename Sink>
 int occupancy_blocks(int dev) {
   static std::atomic<int> cache[kMaxDevices];
   int v = cache[dev].load(std::memory_order_relaxed);
   if (v > 0) return v;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gen_kernel<DIST, T>, kThreads, 0) !=
-          cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gen_kernel<DIST, T, Sink>, kThreads,
+                                                    0) != cudaSuccess ||
       occ < 1) {
     cudaGetLastError();
     occ = 1;
@@ -593,12 +722,47 @@ zig_status launch_gen(void* out, uint64_t n, uint64_t seed, uint64_t offset,
   const uint64_t head = align_elems < n ? align_elems : n;
   const uint64_t nvec = (n - head) / V;
   const uint64_t tiles = (nvec + (uint64_t)kPThreads * R - 1) / ((uint64_t)kPThreads * R);
-  const uint64_t cap = (uint64_t)g_dev[dev].sms * (uint64_t)occupancy_blocks<DIST, T>(dev);
+  const uint64_t cap =
+      (uint64_t)g_dev[dev].sms * (uint64_t)occupancy_blocks<DIST, T, StoreSink<T>>(dev);
   uint64_t grid = tiles < cap ? tiles : cap;
   if (grid < 1) grid = 1;
   Limits lim{g_max_att.load(), g_max_tail.load()};
-  gen_kernel<DIST, T><<<(unsigned)grid, kThreads, 0, stream>>>(
-      (T*)out, n, (uint32_t)head, nvec, seed, offset, round_keys(seed), lim);
+  StoreSink<T> sink{(T*)out, head};
+  gen_kernel<DIST, T, StoreSink<T>><<<(unsigned)grid, kThreads, 0, stream>>>(
+      sink, n, (uint32_t)head, nvec, seed, offset, round_keys(seed), lim, ReduceOut{});
+  if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
+  return ZIG_OK;
+}
+
+// Grid of the fused reduction on device dev (one partial per CTA).
+template <int DIST, typename T>
+uint64_t moment_grid_cap(int dev) {
+  return (uint64_t)g_dev[dev].sms * (uint64_t)occupancy_blocks<DIST, T, MomentSink<T>>(dev);
+}
+
+constexpr size_t kTicketBytes = 256;  // workspace: ticket, then the partials
+
+template <int DIST, typename T>
+zig_status launch_moments(uint64_t n, uint64_t seed, uint64_t offset, double* d_sums,
+                          unsigned long long* d_hist, void* d_ws, size_t ws_bytes,
+                          cudaStream_t stream, int dev) {
+  constexpr int V = GenShape<T>::V, R = GenShape<T>::R;
+  const uint64_t nvec = n / V;
+  const uint64_t tiles = (nvec + (uint64_t)kPThreads * R - 1) / ((uint64_t)kPThreads * R);
+  const uint64_t cap = moment_grid_cap<DIST, T>(dev);
+  uint64_t grid = tiles < cap ? tiles : cap;
+  if (grid < 1) grid = 1;
+  if (ws_bytes < kTicketBytes + grid * 4 * sizeof(double)) return ZIG_E_NOMEM;
+  if (cudaMemsetAsync(d_hist, 0, kBins * sizeof(unsigned long long), stream) != cudaSuccess ||
+      cudaMemsetAsync(d_ws, 0, sizeof(unsigned), stream) != cudaSuccess) {
+    cudaGetLastError();
+    return ZIG_E_CUDA;
+  }
+  Limits lim{g_max_att.load(), g_max_tail.load()};
+  ReduceOut red{d_sums, d_hist, (double*)((char*)d_ws + kTicketBytes), (unsigned*)d_ws};
+  MomentSink<T> sink;
+  gen_kernel<DIST, T, MomentSink<T>><<<(unsigned)grid, kThreads, 0, stream>>>(
+      sink, n, 0u, nvec, seed, offset, round_keys(seed), lim, red);
   if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
   return ZIG_OK;
 }
@@ -697,6 +861,46 @@ zig_status zig_exponential(void* out, uint64_t n, uint64_t seed, uint64_t offset
 zig_status zig_normal(void* out, uint64_t n, uint64_t seed, uint64_t offset, zig_dtype dtype,
                       void* stream) {
   return generate(ZIG_NORMAL, out, n, seed, offset, dtype, stream);
+}
+
+size_t zig_moments_workspace_bytes(zig_dist dist, zig_dtype dtype) {
+  int dev;
+  if (current_device(&dev) != ZIG_OK || !g_dev[dev].ready.load(std::memory_order_acquire))
+    return 0;
+  uint64_t cap;
+  if (dist == ZIG_EXP)
+    cap = dtype == ZIG_F64 ? moment_grid_cap<ZIG_EXP, double>(dev)
+                           : moment_grid_cap<ZIG_EXP, float>(dev);
+  else
+    cap = dtype == ZIG_F64 ? moment_grid_cap<ZIG_NORMAL, double>(dev)
+                           : moment_grid_cap<ZIG_NORMAL, float>(dev);
+  return kTicketBytes + (size_t)cap * 4 * sizeof(double);
+}
+
+zig_status zig_moments(zig_dist dist, zig_dtype dtype, uint64_t n, uint64_t seed,
+                       uint64_t offset, double* d_sums, unsigned long long* d_hist,
+                       void* d_workspace, size_t workspace_bytes, void* stream) {
+  if (dist != ZIG_EXP && dist != ZIG_NORMAL) return ZIG_E_INVAL;
+  if (dtype != ZIG_F32 && dtype != ZIG_F64) return ZIG_E_INVAL;
+  if (d_sums == nullptr || d_hist == nullptr || d_workspace == nullptr) return ZIG_E_INVAL;
+  if ((uintptr_t)d_sums % 8 || (uintptr_t)d_hist % 8 || (uintptr_t)d_workspace % 8)
+    return ZIG_E_ALIGN;
+  if (n > 0 && n - 1 > UINT64_MAX - offset) return ZIG_E_RANGE;
+  if (n > (UINT64_MAX / 16)) return ZIG_E_RANGE;
+  int dev;
+  zig_status st = current_device(&dev);
+  if (st != ZIG_OK) return st;
+  if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dist == ZIG_EXP)
+    return dtype == ZIG_F64 ? launch_moments<ZIG_EXP, double>(n, seed, offset, d_sums, d_hist,
+                                                              d_workspace, workspace_bytes, s, dev)
+                            : launch_moments<ZIG_EXP, float>(n, seed, offset, d_sums, d_hist,
+                                                             d_workspace, workspace_bytes, s, dev);
+  return dtype == ZIG_F64 ? launch_moments<ZIG_NORMAL, double>(n, seed, offset, d_sums, d_hist,
+                                                               d_workspace, workspace_bytes, s, dev)
+                          : launch_moments<ZIG_NORMAL, float>(n, seed, offset, d_sums, d_hist,
+                                                              d_workspace, workspace_bytes, s, dev);
 }
 
 zig_status zig_status_poll(void* stream) {

@@ -1,0 +1,92 @@
+"""GPU parity of the fused generate-and-reduce path (zig_moments).
+
+The variates are those of zig_normal/zig_exponential on the same counters
+(themselves checked element by element), so the oracle's plain definitions
+apply: the histogram must equal the oracle's exactly; each power sum must
+be within the rounding bound of its accumulation scheme (FP32 partials of
+at most 16 terms plus FP64 accumulation):
+|S_gpu - S| <= 20 * 2^-24 * sum |x|^k (FP32) or 1e-12 * sum |x|^k (FP64).
+At the full 2^34 size: moments within 5 standard errors of the closed
+forms and the histogram against the exact bin probabilities.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def zig():
+    assert torch.cuda.is_available()
+    from paper_1403_6870_gb300 import build
+
+    build.build()
+    import paper_1403_6870_gb300 as z
+
+    z.zig_build_tables()
+    return z
+
+
+def _run(z, dist, dtype, n, seed, offset):
+    sums = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    hist = torch.full((4098,), -1, dtype=torch.int64, device="cuda")
+    ws = torch.empty(z.zig_moments_workspace_bytes(dist, dtype), dtype=torch.uint8, device="cuda")
+    z.zig_moments(dist, dtype, n, seed, offset, sums, hist, ws)
+    return sums.cpu().numpy(), hist.cpu().numpy().astype(np.uint64)
+
+
+@pytest.mark.parametrize("dist,dtype", [(1, 0), (0, 0), (1, 1), (0, 1)])
+def test_moments_match_oracle(zig, orc, dist, dtype):
+    n, seed, off = (1 << 22) + 333, 0x9E3779B97F4A7C15, 4321
+    for rep in range(2):  # twice: the workspace ticket must reset
+        sums, hist = _run(zig, dist, dtype, n, seed, off)
+        assert zig.zig_status_poll() == zig.ZIG_OK
+        ref, abss, rhist, errs = orc.moments(dist, dtype, seed, off, n)
+        assert errs == 0
+        assert np.array_equal(hist, rhist)
+        assert int(hist.sum()) == n
+        tol = (20 * 2.0**-24 if dtype == 0 else 1e-12) * abss + 1e-300
+        assert np.all(np.abs(sums - ref) <= tol), (sums, ref, tol)
+
+
+def test_moments_small_and_edge_sizes(zig, orc):
+    for n in (1, 7, 1000, 3584 * 7 + 5):
+        sums, hist = _run(zig, 1, 0, n, W.SEED, 17)
+        ref, abss, rhist, _ = orc.moments(1, 0, W.SEED, 17, n)
+        assert np.array_equal(hist, rhist)
+        assert np.all(np.abs(sums - ref) <= 20 * 2.0**-24 * abss + 1e-300)
+
+
+def test_workspace_too_small(zig):
+    sums = torch.zeros(4, dtype=torch.float64, device="cuda")
+    hist = torch.zeros(4098, dtype=torch.int64, device="cuda")
+    ws = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(zig.ZigError) as e:
+        zig.zig_moments(1, 0, 1 << 24, 1, 0, sums, hist, ws)
+    assert e.value.status == zig.ZIG_E_NOMEM
+
+
+def test_fused_2p34_normal_f32(zig):
+    c = W.WORKLOADS["normal_f32_fused_2p34"]
+    n = c["n"]
+    sums, hist = _run(zig, c["dist"], c["dtype"], n, W.SEED, c["offset"])
+    assert zig.zig_status_poll() == zig.ZIG_OK
+    assert int(hist.sum()) == n
+    m = sums / n
+    for k, (mu, var) in enumerate(zip((0, 1, 0, 3), (1, 2, 15, 96))):
+        assert abs(m[k] - mu) < 5 * math.sqrt(var / n), (k, m[k])
+    from scipy import special
+
+    edges = (np.arange(4097) - 2048) / 256.0
+    p = np.diff(special.ndtr(edges))
+    p = np.concatenate([p, [special.ndtr(-8.0), special.ndtr(-8.0)]])
+    e = n * p
+    ok = e > 50
+    chi2 = float(((hist[ok].astype(np.float64) - e[ok]) ** 2 / e[ok]).sum())
+    df = int(ok.sum()) - 1
+    assert abs(chi2 - df) < 6 * math.sqrt(2 * df), (chi2, df)
