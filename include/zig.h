@@ -176,6 +176,34 @@ zig_status zig_moments(zig_dist dist, zig_dtype dtype, uint64_t n,
                        size_t workspace_bytes, void* stream);
 
 /*
+ * zig_moments_noalloc -- zig_moments without a caller workspace.
+ *
+ * The paper has no counterpart; this is a service for callers that cannot
+ * allocate device memory at all: code handed only its output buffers by a
+ * host application or inference server that owns the device's memory,
+ * code running where the surrounding framework forbids allocation (a
+ * locked or exhausted pool, a region whose memory layout must stay fixed),
+ * and latency-critical paths that may not enter the allocator.  It computes
+ * exactly what zig_moments computes and allocates nothing: no cudaMalloc,
+ * no cudaFree, no library routine that allocates.
+ *
+ * Its scratch (a ticket and 4 FP64 partials per thread block) is a static
+ * device array of 64 KiB in the library, present on every device that
+ * loads the library until the process exits; its device address is taken
+ * by zig_build_tables, which must have run on the current device (as for
+ * every entry point).  All calls share that array and it keeps the last
+ * call's contents; each call clears the part that must start at zero.
+ * Calls whose executions overlap on the GPU (any device-side concurrency,
+ * e.g. two streams) race on the array and give wrong results: serialise
+ * them.  A device that would need more than the 64 KiB (more than 2040
+ * thread blocks at once) gets ZIG_E_NOMEM; otherwise the returns are
+ * those of zig_moments.
+ */
+zig_status zig_moments_noalloc(zig_dist dist, zig_dtype dtype, uint64_t n,
+                               uint64_t seed, uint64_t offset, double* d_sums,
+                               unsigned long long* d_hist, void* stream);
+
+/*
  * zig_status_poll -- read and clear this device's status word.
  * Synchronises stream first.  Returns ZIG_OK if no device-side condition
  * was recorded since the last poll, ZIG_E_LOOP_LIMIT if a fringe loop hit

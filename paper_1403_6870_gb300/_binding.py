@@ -67,6 +67,8 @@ _status_poll = _sig("zig_status_poll", _int, [_vp])
 _moments_ws = _sig("zig_moments_workspace_bytes", ctypes.c_size_t, [_int, _int])
 _moments = _sig("zig_moments", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp, _vp,
                                       ctypes.c_size_t, _vp])
+_moments_noalloc = _sig("zig_moments_noalloc", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp,
+                                                      _vp])
 _set_limits = _sig("zig_set_fringe_limits", _int, [_int, _int])
 
 
@@ -156,6 +158,21 @@ def zig_moments(dist: int, dtype: int, n: int, seed: int, offset: int, sums, his
     _check(_moments(int(dist), int(dtype), n, seed & (2**64 - 1), offset & (2**64 - 1),
                     sums.data_ptr(), hist.data_ptr(), workspace.data_ptr(), wbytes,
                     _stream_handle(stream, sums)), "zig_moments")
+
+
+def zig_moments_noalloc(dist: int, dtype: int, n: int, seed: int, offset: int, sums, hist,
+                        stream=None) -> None:
+    """zig_moments with the library's static scratch instead of a workspace,
+    for callers that cannot allocate device memory (see include/zig.h)."""
+    import torch
+
+    if sums.dtype != torch.float64 or sums.numel() < 4 or not sums.is_cuda:
+        raise ValueError("sums must be a CUDA float64 tensor of 4 elements")
+    if hist.element_size() != 8 or hist.numel() < 4098 or not hist.is_cuda:
+        raise ValueError("hist must be a CUDA 64-bit integer tensor of 4098 elements")
+    _check(_moments_noalloc(int(dist), int(dtype), n, seed & (2**64 - 1), offset & (2**64 - 1),
+                            sums.data_ptr(), hist.data_ptr(), _stream_handle(stream, sums)),
+           "zig_moments_noalloc")
 
 
 def zig_status_poll(stream=None) -> int:

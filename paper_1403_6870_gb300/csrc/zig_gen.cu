@@ -464,6 +464,14 @@ __device__ __forceinline__ unsigned producer_tile(Sink& sink, uint64_t g0, uint6
   return fm;
 }
 
+// Scratch of zig_moments_noalloc: the same layout as a caller workspace
+// (a 256-byte ticket area, then 4 FP64 partials per CTA), in static device
+// memory that every device loading the library holds until exit.  Host
+// code must not pass the symbol itself to a kernel: its device address is
+// taken once per device with cudaGetSymbolAddress in zig_build_tables.
+constexpr size_t kStaticScratchBytes = 64 * 1024;
+static __device__ __align__(256) unsigned char g_moment_scratch[kStaticScratchBytes];
+
 // Where the fused reduction's partial results go: per-CTA FP64 partials
 // in a caller workspace, the last CTA to finish sums them in CTA order.
 struct ReduceOut {
@@ -635,6 +643,7 @@ std::atomic<int> g_max_tail{16};
 struct DeviceState {
   std::atomic<bool> ready{false};
   unsigned int* d_status = nullptr;
+  void* d_static_scratch = nullptr;  // device address of g_moment_scratch
   int sms = 0;
 };
 DeviceState g_dev[kMaxDevices];
@@ -830,9 +839,11 @@ zig_status zig_build_tables(void) {
   to_device_layout(g_host[0], &h[0]);
   to_device_layout(g_host[1], &h[1]);
   void* status = nullptr;
+  void* scratch = nullptr;
   int sms = 0;
   if (cudaMemcpyToSymbol(g_tab, h, sizeof(h)) != cudaSuccess ||
       cudaGetSymbolAddress(&status, g_status) != cudaSuccess ||
+      cudaGetSymbolAddress(&scratch, g_moment_scratch) != cudaSuccess ||
       cudaMemset(status, 0, sizeof(unsigned int)) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
@@ -840,6 +851,7 @@ zig_status zig_build_tables(void) {
     return ZIG_E_CUDA;
   }
   g_dev[dev].d_status = (unsigned int*)status;
+  g_dev[dev].d_static_scratch = scratch;
   g_dev[dev].sms = sms;
   g_dev[dev].ready.store(true, std::memory_order_release);
   return ZIG_OK;
@@ -901,6 +913,20 @@ zig_status zig_moments(zig_dist dist, zig_dtype dtype, uint64_t n, uint64_t seed
                                                                d_workspace, workspace_bytes, s, dev)
                           : launch_moments<ZIG_NORMAL, float>(n, seed, offset, d_sums, d_hist,
                                                               d_workspace, workspace_bytes, s, dev);
+}
+
+zig_status zig_moments_noalloc(zig_dist dist, zig_dtype dtype, uint64_t n, uint64_t seed,
+                               uint64_t offset, double* d_sums, unsigned long long* d_hist,
+                               void* stream) {
+  int dev;
+  zig_status st = current_device(&dev);
+  if (st != ZIG_OK) return st;
+  if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
+  const size_t need = zig_moments_workspace_bytes(dist, dtype);
+  if (need == 0) return ZIG_E_INVAL;
+  if (need > kStaticScratchBytes) return ZIG_E_NOMEM;  // device needs more blocks than it holds
+  return zig_moments(dist, dtype, n, seed, offset, d_sums, d_hist,
+                     g_dev[dev].d_static_scratch, kStaticScratchBytes, stream);
 }
 
 zig_status zig_status_poll(void* stream) {
