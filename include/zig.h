@@ -204,10 +204,58 @@ zig_status zig_moments_noalloc(zig_dist dist, zig_dtype dtype, uint64_t n,
                                unsigned long long* d_hist, void* stream);
 
 /*
+ * Batched requests: many generation calls served by one persistent launch.
+ * Each request asks for n variates of its own distribution and precision,
+ * under its own Philox key and counter offset (element t of request r is
+ * the variate of counter offset_r + t, exactly as zig_exponential /
+ * zig_normal would write it before the transform), then transformed:
+ *   exponential with rate lambda = p0 > 0:   x * RN(1 / lambda);
+ *   normal with mean mu = p0, sd sigma = p1 > 0:  fma(sigma, z, mu);
+ * FP32 requests use RN32(RN64(1/lambda)), RN32(mu), RN32(sigma) and binary32
+ * arithmetic.  The paper's method has no batched interface; the transforms
+ * are the standard scale and location changes of Exp(1) and N(0, 1).
+ */
+typedef struct zig_request {
+  void* out;       /* device array of n float (ZIG_F32) or double elements */
+  uint64_t n;      /* < 2^40 */
+  uint64_t seed;   /* Philox key */
+  uint64_t offset; /* counter of element 0; offset + n must not pass 2^64 */
+  uint32_t dist;   /* zig_dist */
+  uint32_t dtype;  /* zig_dtype */
+  double p0;       /* exponential: rate; normal: mean */
+  double p1;       /* normal: standard deviation; exponential: unused */
+} zig_request;
+
+/* Bytes of workspace zig_batch needs for count requests. */
+size_t zig_batch_workspace_bytes(uint32_t count);
+
+/* Host-side check of a request array (the device checks the same rules and
+ * skips a failing request, flagging ZIG_E_INVAL in the status word).
+ * Returns ZIG_OK or ZIG_E_INVAL, ZIG_E_ALIGN, ZIG_E_RANGE for the first
+ * failing request. */
+zig_status zig_batch_validate(const zig_request* h_reqs, uint32_t count);
+
+/*
+ * zig_batch -- serve count requests (device array d_reqs, count < 2^23)
+ * with one prep kernel and one persistent kernel on stream.  d_workspace is
+ * caller-owned device scratch of zig_batch_workspace_bytes(count) bytes
+ * (16-byte aligned).  d_done_ns (nullable, device, count entries) receives,
+ * per request, the nanoseconds from the batch start (end of the prep
+ * kernel) until its last output was written.  The call does not allocate
+ * or synchronise.  Calls on the same workspace must not overlap.  Returns
+ * ZIG_OK, ZIG_E_INVAL, ZIG_E_NOMEM (workspace too small), ZIG_E_ALIGN,
+ * ZIG_E_NOTINIT or ZIG_E_CUDA.
+ */
+zig_status zig_batch(const zig_request* d_reqs, uint32_t count,
+                     unsigned long long* d_done_ns, void* d_workspace,
+                     size_t workspace_bytes, void* stream);
+
+/*
  * zig_status_poll -- read and clear this device's status word.
  * Synchronises stream first.  Returns ZIG_OK if no device-side condition
  * was recorded since the last poll, ZIG_E_LOOP_LIMIT if a fringe loop hit
- * its cap (those outputs are NaN), ZIG_E_TIMEOUT if a kernel's internal
+ * its cap (those outputs are NaN), ZIG_E_INVAL if zig_batch skipped an
+ * invalid request, ZIG_E_TIMEOUT if a kernel's internal
  * wait between its warps gave up after 20 s (its outputs are then
  * incomplete), ZIG_E_NOTINIT or ZIG_E_CUDA.
  */

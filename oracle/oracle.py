@@ -124,6 +124,17 @@ def lib():
             L.orc_moments.restype = ctypes.c_int64
             L.orc_enum_overhang.argtypes = [P(Tables), ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
             L.orc_enum_overhang.restype = ctypes.c_int64
+            L.orc_transform64.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double]
+            L.orc_transform64.restype = ctypes.c_double
+            L.orc_transform32.argtypes = [ctypes.c_int, ctypes.c_float, ctypes.c_double,
+                                          ctypes.c_double]
+            L.orc_transform32.restype = ctypes.c_float
+            L.orc_request_values.argtypes = [P(Tables), P(Tables), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_void_p, ctypes.c_uint64,
+                                             ctypes.c_void_p, ctypes.c_int]
+            L.orc_request_values.restype = ctypes.c_int64
         return _lib
 
 
@@ -236,3 +247,22 @@ def enum_overhang(t: Tables, j: int, bits: int) -> np.ndarray:
     buf = np.empty(1 << (2 * bits), dtype=np.float64)
     cnt = lib().orc_enum_overhang(ctypes.byref(t), j, bits, buf.ctypes.data)
     return buf[:cnt].copy()
+
+
+def request_values(req: dict, idx) -> np.ndarray:
+    """Transformed variates of one batched request at positions idx (float64;
+    FP32 results widened exactly)."""
+    idx = np.ascontiguousarray(idx, dtype=np.uint64)
+    out = np.empty(idx.size, dtype=np.float64)
+    te, tn = tables(EXP), tables(NORMAL)
+    lib().orc_request_values(ctypes.byref(te), ctypes.byref(tn), req["dist"], req["dtype"],
+                             req["seed"] & (2**64 - 1), req["offset"] & (2**64 - 1),
+                             float(req["p0"]), float(req["p1"]), idx.ctypes.data, idx.size,
+                             out.ctypes.data, default_threads())
+    return out
+
+
+def transform(dist: int, dtype: int, x: float, p0: float, p1: float) -> float:
+    if dtype == F64:
+        return float(lib().orc_transform64(dist, x, p0, p1))
+    return float(lib().orc_transform32(dist, x, p0, p1))

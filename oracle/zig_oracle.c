@@ -750,3 +750,32 @@ int64_t orc_enum_overhang(const orc_tables* t, int j, int bits, double* xs) {
   }
   return cnt;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Batched requests: parameter transforms                                   */
+/* ------------------------------------------------------------------------ */
+double orc_transform64(int dist, double x, double p0, double p1) {
+  if (dist == ORC_EXP) return x * (1.0 / p0);
+  return fma(p1, x, p0);
+}
+
+float orc_transform32(int dist, float x, double p0, double p1) {
+  if (dist == ORC_EXP) return x * (float)(1.0 / p0);
+  return fmaf((float)p1, x, (float)p0);
+}
+
+int64_t orc_request_values(const orc_tables* te, const orc_tables* tn, int dist, int dtype,
+                           uint64_t seed, uint64_t offset, double p0, double p1,
+                           const uint64_t* idx, uint64_t m, double* out, int nthreads) {
+  int64_t errs;
+  if (dtype == ORC_F64) {
+    errs = orc_fill(te, tn, dist, dtype, seed, offset, m, idx, out, NULL, NULL, nthreads);
+    for (uint64_t k = 0; k < m; k++) out[k] = orc_transform64(dist, out[k], p0, p1);
+  } else {
+    float* tmp = (float*)malloc(m * sizeof(float));
+    errs = orc_fill(te, tn, dist, dtype, seed, offset, m, idx, tmp, NULL, NULL, nthreads);
+    for (uint64_t k = 0; k < m; k++) out[k] = (double)orc_transform32(dist, tmp[k], p0, p1);
+    free(tmp);
+  }
+  return errs;
+}

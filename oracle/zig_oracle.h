@@ -168,6 +168,19 @@ int64_t orc_moments(const orc_tables* te, const orc_tables* tn, int dist,
  * (capacity 4^bits) and returns their count. */
 int64_t orc_enum_overhang(const orc_tables* t, int j, int bits, double* xs);
 
+/* Batched requests: the parameter transform of a request's variate x
+ * (exponential with rate lambda: x * RN(1/lambda); normal with mean mu and
+ * standard deviation sigma: fma(sigma, x, mu)); FP32 requests use
+ * RN32(RN64(1/lambda)), RN32(mu), RN32(sigma) and binary32 arithmetic. */
+double orc_transform64(int dist, double x, double p0, double p1);
+float orc_transform32(int dist, float x, double p0, double p1);
+
+/* out[k] = transformed variate k' = idx[k] of a request (dist, dtype, seed,
+ * offset, p0, p1); values as double (FP32 results widened exactly). */
+int64_t orc_request_values(const orc_tables* te, const orc_tables* tn, int dist, int dtype,
+                           uint64_t seed, uint64_t offset, double p0, double p1,
+                           const uint64_t* idx, uint64_t m, double* out, int nthreads);
+
 size_t orc_tables_size(void);
 
 #ifdef __cplusplus

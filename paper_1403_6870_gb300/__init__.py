@@ -14,7 +14,8 @@ def __getattr__(name):
     global _binding
     # only API names load the binding; anything else (e.g. the `build`
     # submodule) falls through to the normal import machinery
-    if not (name.startswith(("zig_", "ZIG_", "Zig")) or name in ("raw_call", "LIB_PATH")):
+    if not (name.startswith(("zig_", "ZIG_", "Zig")) or
+            name in ("raw_call", "LIB_PATH", "pack_requests", "request_dtype")):
         raise AttributeError(name)
     if _binding is None:
         _binding = importlib.import_module("._binding", __name__)

@@ -67,6 +67,9 @@ _status_poll = _sig("zig_status_poll", _int, [_vp])
 _moments_ws = _sig("zig_moments_workspace_bytes", ctypes.c_size_t, [_int, _int])
 _moments = _sig("zig_moments", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp, _vp,
                                       ctypes.c_size_t, _vp])
+_batch_ws = _sig("zig_batch_workspace_bytes", ctypes.c_size_t, [ctypes.c_uint32])
+_batch_validate = _sig("zig_batch_validate", _int, [_vp, ctypes.c_uint32])
+_batch = _sig("zig_batch", _int, [_vp, ctypes.c_uint32, _vp, _vp, ctypes.c_size_t, _vp])
 _moments_noalloc = _sig("zig_moments_noalloc", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp,
                                                       _vp])
 _set_limits = _sig("zig_set_fringe_limits", _int, [_int, _int])
@@ -175,10 +178,54 @@ def zig_moments_noalloc(dist: int, dtype: int, n: int, seed: int, offset: int, s
            "zig_moments_noalloc")
 
 
+REQUEST_DTYPE = None
+
+
+def request_dtype():
+    """numpy structured dtype laid out like zig_request (56 bytes)."""
+    global REQUEST_DTYPE
+    if REQUEST_DTYPE is None:
+        import numpy as np
+
+        REQUEST_DTYPE = np.dtype([("out", "<u8"), ("n", "<u8"), ("seed", "<u8"), ("offset", "<u8"),
+                                  ("dist", "<u4"), ("dtype", "<u4"), ("p0", "<f8"), ("p1", "<f8")])
+        assert REQUEST_DTYPE.itemsize == 56
+    return REQUEST_DTYPE
+
+
+def pack_requests(reqs) -> "numpy.ndarray":
+    """Pack dicts with keys out (device address), n, seed, offset, dist,
+    dtype, p0, p1 into a zig_request array (host memory)."""
+    import numpy as np
+
+    a = np.zeros(len(reqs), dtype=request_dtype())
+    for k, q in enumerate(reqs):
+        a[k] = (int(q["out"]), int(q["n"]), int(q["seed"]) & (2**64 - 1),
+                int(q["offset"]) & (2**64 - 1), int(q["dist"]), int(q["dtype"]),
+                float(q["p0"]), float(q["p1"]))
+    return a
+
+
+def zig_batch_workspace_bytes(count: int) -> int:
+    return int(_batch_ws(int(count)))
+
+
+def zig_batch_validate(h_reqs) -> int:
+    """Host-side check of a packed request array; returns the status code."""
+    return int(_batch_validate(h_reqs.ctypes.data, len(h_reqs)))
+
+
+def zig_batch(d_reqs, count: int, workspace, done_ns=None, stream=None) -> None:
+    """Serve `count` packed requests held in the device tensor d_reqs."""
+    wbytes = workspace.numel() * workspace.element_size()
+    _check(_batch(d_reqs.data_ptr(), int(count), None if done_ns is None else done_ns.data_ptr(),
+                  workspace.data_ptr(), wbytes, _stream_handle(stream, workspace)), "zig_batch")
+
+
 def zig_status_poll(stream=None) -> int:
     """Returns the device status (ZIG_OK or ZIG_E_LOOP_LIMIT) and clears it."""
     st = _status_poll(_stream_handle(stream))
-    if st not in (ZIG_OK, ZIG_E_LOOP_LIMIT, ZIG_E_TIMEOUT):
+    if st not in (ZIG_OK, ZIG_E_LOOP_LIMIT, ZIG_E_TIMEOUT, ZIG_E_INVAL):
         raise ZigError(st, "zig_status_poll")
     return st
 
@@ -187,7 +234,7 @@ def zig_set_fringe_limits(max_attempts: int = 64, max_tail: int = 16) -> None:
     _check(_set_limits(int(max_attempts), int(max_tail)), "zig_set_fringe_limits")
 
 
-def raw_call(name: str, *args) -> int:
+def raw_call(name: str, *args) -> int:  # noqa: C901
     """Call an exported function with raw C arguments and return its status
     (used to exercise argument checks without raising)."""
     table = {"zig_exponential": _exponential, "zig_normal": _normal, "zig_moments": _moments,

@@ -149,6 +149,21 @@ struct RunState {
   }
 };
 
+// Round keys of a key, computed on the device (the batch kernel's requests
+// each carry their own key).
+__device__ __forceinline__ RoundKeys device_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0;
+    rk.k1[r] = k1;
+    k0 += kW0;
+    k1 += kW1;
+  }
+  return rk;
+}
+
 // Shared state of one CTA.
 template <typename T>
 struct CtaState {
@@ -169,8 +184,8 @@ struct CtaState {
 // its fence, which comes before its ring writes, so the consumer's later
 // patch of the same address is ordered after them.  Returns false if the
 // wait gave up.
-template <typename T, typename PosFn>
-__device__ __forceinline__ bool publish(CtaState<T>& sh, int cnt, PosFn pos) {
+template <typename State, typename PosFn>
+__device__ __forceinline__ bool publish(State& sh, int cnt, PosFn pos) {
   const int lane = threadIdx.x & 31;
   int incl = cnt;
 #pragma unroll
@@ -307,19 +322,24 @@ __device__ __forceinline__ int claim(bool f, int& n) {
   return k;
 }
 
-// Stage 1 (one fringe position per lane): steps 3-7 for the first attempt.
+// Queue values.  An item is a queued value, possibly with kWholeTag (the
+// draw needs the whole sampler); the value's bits under kPosMask are the
+// output position (the batch kernel keeps a request index above them).
+// Sinks receive the value.
+//
+// Stage 1 (one fringe item per lane): steps 3-7 for the first attempt.
 // Block 0 gives U_1 (as ux) and the alias word; block 1's first word gives
 // uy.  Tail draws (j = 0) and whole-sampler items go to the tail queue;
 // rejected attempts to the retry queue with their state.
-template <int DIST, typename T, typename Sink>
+template <int DIST, typename T, uint64_t kPosMask, typename Sink, typename State>
 __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const RoundKeys& rk,
-                                          Limits lim, bool active, uint64_t item,
-                                          CtaState<T>& sh, SideCounts& c) {
+                                          Limits lim, bool active, uint64_t item, State& sh,
+                                          SideCounts& c) {
   typedef Prec<T> P;
   const DevTab& t = g_tab[DIST];
   const bool whole = (item & kWholeTag) != 0;
-  const uint64_t p = item & ~kWholeTag;
-  const uint64_t g = offset + p;
+  const uint64_t p = item & ~kWholeTag;  // the queued value
+  const uint64_t g = offset + (p & kPosMask);
   const uint4 b0 = philox_block(g, 0u, rk);
   const uint64_t w0 = pack(b0.x, b0.y);
   const int j = alias_pick(t, pack(b0.z, b0.w));
@@ -357,10 +377,10 @@ __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const Rou
 // is kept (Table 1 step 8 returns to step 4).  State: j in bits 0-7, the
 // normal's sign in bit 8, completed attempts in bits 9-31, next block in
 // bits 32-63.
-template <int DIST, typename T, typename Sink>
+template <int DIST, typename T, uint64_t kPosMask, typename Sink, typename State>
 __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const RoundKeys& rk,
                                             Limits lim, bool active, uint64_t p,
-                                            uint64_t state, uint64_t word, CtaState<T>& sh,
+                                            uint64_t state, uint64_t word, State& sh,
                                             SideCounts& c) {
   typedef Prec<T> P;
   const DevTab& t = g_tab[DIST];
@@ -371,7 +391,7 @@ __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const R
   bool retry = false;
   uint64_t nstate = 0, next = 0;
   if (active) {
-    const uint4 b = philox_block(offset + p, blk, rk);
+    const uint4 b = philox_block(offset + (p & kPosMask), blk, rk);
     T x;
     if (overhang_attempt<DIST, T>(t, j, P::ubits(word), P::ubits(pack(b.x, b.y)), x)) {
       put_signed<DIST, T>(sink, p, x, negative);
@@ -395,10 +415,11 @@ __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const R
 // Consumer: run the retry and tail stages while they hold `need` or more
 // entries (at most 32 per batch).  Each side queue holds fewer than 32
 // entries before a stage-1 batch, so it stays within its 64 slots.
-template <int DIST, typename T, typename Sink>
+template <int DIST, typename T, typename Sink, typename State>
 __device__ __forceinline__ void side_stages(Sink& sink, uint64_t seed, uint64_t offset,
                                             const RoundKeys& rk, Limits lim, int need,
-                                            CtaState<T>& sh, SideCounts& c) {
+                                            State& sh, SideCounts& c) {
+  constexpr uint64_t kPos = ~kWholeTag;
   const int lane = threadIdx.x & 31;
   for (;;) {
     if (c.retry >= need) {
@@ -409,7 +430,7 @@ __device__ __forceinline__ void side_stages(Sink& sink, uint64_t seed, uint64_t 
                      w = active ? sh.rw[k] : 0;
       c.retry -= take;
       __syncwarp();  // slots read before they are refilled
-      stage_retry<DIST, T>(sink, offset, rk, lim, active, p, st, w, sh, c);
+      stage_retry<DIST, T, kPos>(sink, offset, rk, lim, active, p, st, w, sh, c);
     } else if (c.tail >= need) {
       const int take = c.tail < 32 ? c.tail : 32;
       const bool active = lane < take;
@@ -481,60 +502,52 @@ struct ReduceOut {
   unsigned* ticket;               // workspace: CTAs finished (zero before launch)
 };
 
-// One launch covers outputs [0, n): a head of < V elements up to the first
-// V-element-aligned address, nvec aligned V-vectors, then a tail of < V
-// elements; head and tail are published by CTA 0 for the whole sampler.
-// Tile t covers vectors [t kTile, (t + 1) kTile); producer thread pt makes
-// vectors t kTile + r kPThreads + pt, r < R.
-template <int DIST, typename T, typename Sink>
-__global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
-    gen_kernel(Sink sink, uint64_t n, uint32_t head, uint64_t nvec, uint64_t seed,
-               uint64_t offset, const RoundKeys rk, Limits lim, ReduceOut red) {
+// One CTA's share of a generation over outputs [0, n): a head of < V
+// elements up to the first V-element-aligned address, nvec aligned
+// V-vectors, then a tail of < V elements.  Tile t covers vectors
+// [t kTile, (t + 1) kTile); producer thread pt makes vectors
+// t kTile + r kPThreads + pt, r < R.  This CTA takes tiles tile, tile + step,
+// ... below tile_end; if `ends`, its warp 0 also publishes the head and tail
+// elements for the whole sampler.  Producer warps return after publishing
+// their last tile (counting themselves in sh.done); the consumer warp
+// returns once every published item has its final value, with sh.done
+// reset to zero and its ring cursor hd advanced past the items.  Returns
+// false if a bounded wait gave up.
+template <int DIST, typename T, typename Sink, typename State>
+__device__ __forceinline__ bool gen_tiles(State& sh, Sink& sink, const T* sX, uint64_t n,
+                                          uint64_t head, uint64_t nvec, uint64_t seed,
+                                          uint64_t offset, const RoundKeys& rk, Limits lim,
+                                          uint64_t tile, uint64_t tile_end, uint64_t step,
+                                          bool ends, unsigned& hd) {
   constexpr int V = GenShape<T>::V, R = GenShape<T>::R, S = V * R;
   constexpr int kTile = kPThreads * R;
-  __shared__ CtaState<T> sh;
-  __shared__ unsigned shist[Sink::kReduce ? kBins : 1];
-
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  for (int k = tid; k < 256; k += kThreads) sh.sX[k] = Prec<T>::X(g_tab[DIST], k);
-  for (int k = tid; k < kRing; k += kThreads) sh.ring[k] = kEmpty;
-  if (Sink::kReduce)
-    for (int k = tid; k < kBins; k += kThreads) shist[k] = 0u;
-  if (tid == 0) {
-    sh.tail = 0;
-    sh.head = 0;
-    sh.done = 0;
-  }
-  if constexpr (Sink::kReduce) sink.init(shist);
-  __syncthreads();
-
+  bool ok = true;
   if (tid < kPThreads) {
     // ---------------- producer warps: steps 1-2 only ----------------
     const uint32_t L = (uint32_t)g_tab[DIST].L;
     const uint64_t body_end = head + nvec * V;
-    bool ok = true;
-    if (blockIdx.x == 0 && tid < 32) {
+    if (ends && tid < 32) {
       // head and tail elements (fewer than V each) take the whole sampler
-      const int hc = (uint32_t)lane < head ? 1 : 0;
+      const int hc = (uint64_t)lane < head ? 1 : 0;
       const int tc = (uint64_t)lane < n - body_end ? 1 : 0;
       ok = publish(sh, hc + tc, [&](int k) {
         return kWholeTag | ((k == 0 && hc) ? (uint64_t)lane : body_end + (uint64_t)lane);
       });
     }
-    const uint64_t ntiles = (nvec + kTile - 1) / kTile;
     constexpr uint32_t kSpan = (uint32_t)((R - 1) * kPThreads * V + (V - 1));
     static_assert(32 * S <= kRing, "a warp's reservation must fit the ring");
-    for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+    for (; ok && tile < tile_end; tile += step) {
       const uint64_t v0 = tile * kTile + (uint64_t)tid;  // this thread's first vector
       const uint64_t p0 = head + v0 * V;                   // and its first position
       const uint64_t g0 = offset + p0;
       const bool full = (tile + 1) * kTile <= nvec;
       unsigned fm;  // outputs of this thread whose layer index is >= L_max
       if ((uint32_t)g0 <= 0xFFFFFFFFu - kSpan)
-        fm = producer_tile<DIST, T, true>(sink, g0, v0, nvec, full, rk, sh.sX, L);
+        fm = producer_tile<DIST, T, true>(sink, g0, v0, nvec, full, rk, sX, L);
       else
-        fm = producer_tile<DIST, T, false>(sink, g0, v0, nvec, full, rk, sh.sX, L);
+        fm = producer_tile<DIST, T, false>(sink, g0, v0, nvec, full, rk, sX, L);
       if (__any_sync(0xFFFFFFFFu, fm != 0)) {
         const unsigned fmask = fm;
         ok = publish(sh, __popc(fmask), [&](int k) {
@@ -550,7 +563,6 @@ __global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
     if (lane == 0) atomicAdd(&sh.done, 1u);
   } else {
     // ---------------- consumer warp: steps 3-8 in stages ----------------
-    unsigned hd = 0;
     SideCounts c{0, 0};
     unsigned long long t0 = globaltimer();
     for (;;) {
@@ -572,6 +584,7 @@ __global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
         state = __shfl_sync(0xFFFFFFFFu, state, 0);
         if (state == 2) {
           if (lane == 0) atomicOr(&g_status, kWaitBit);
+          ok = false;
           break;
         }
         if (state == 0) {
@@ -587,13 +600,47 @@ __global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
       __threadfence_block();
       __syncwarp();
       if (lane == 0) *(volatile unsigned*)&sh.head = hd;
-      stage_new<DIST, T>(sink, offset, rk, lim, active, active ? item : 0, sh, c);
+      stage_new<DIST, T, ~kWholeTag>(sink, offset, rk, lim, active, active ? item : 0, sh, c);
       __syncwarp();
       side_stages<DIST, T>(sink, seed, offset, rk, lim, last ? 1 : 32, sh, c);
       if (last) break;
       t0 = globaltimer();
     }
+    // the producers have all counted themselves; none touches sh.done again
+    // before the caller's next barrier
+    if (lane == 0) sh.done = 0u;
   }
+  return ok;
+}
+
+// One launch covers outputs [0, n) (layout as in gen_tiles); CTA b takes
+// tiles b, b + gridDim.x, ... and CTA 0 the head and tail elements.
+template <int DIST, typename T, typename Sink>
+__global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
+    gen_kernel(Sink sink, uint64_t n, uint32_t head, uint64_t nvec, uint64_t seed,
+               uint64_t offset, const RoundKeys rk, Limits lim, ReduceOut red) {
+  constexpr int R = GenShape<T>::R;
+  constexpr int kTile = kPThreads * R;
+  __shared__ CtaState<T> sh;
+  __shared__ unsigned shist[Sink::kReduce ? kBins : 1];
+
+  const int tid = threadIdx.x;
+  for (int k = tid; k < 256; k += kThreads) sh.sX[k] = Prec<T>::X(g_tab[DIST], k);
+  for (int k = tid; k < kRing; k += kThreads) sh.ring[k] = kEmpty;
+  if (Sink::kReduce)
+    for (int k = tid; k < kBins; k += kThreads) shist[k] = 0u;
+  if (tid == 0) {
+    sh.tail = 0;
+    sh.head = 0;
+    sh.done = 0;
+  }
+  if constexpr (Sink::kReduce) sink.init(shist);
+  __syncthreads();
+
+  const uint64_t ntiles = (nvec + kTile - 1) / kTile;
+  unsigned hd = 0;
+  gen_tiles<DIST, T>(sh, sink, sh.sX, n, head, nvec, seed, offset, rk, lim, blockIdx.x, ntiles,
+                     gridDim.x, blockIdx.x == 0, hd);
 
   if constexpr (Sink::kReduce) {
     // CTA partials in thread order, then the CTA's histogram into the
@@ -626,6 +673,12 @@ __global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
     }
   }
 }
+
+}  // namespace zig
+
+#include "zig_batch.cuh"
+
+namespace zig {
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -773,6 +826,38 @@ zig_status launch_moments(uint64_t n, uint64_t seed, uint64_t offset, double* d_
   gen_kernel<DIST, T, MomentSink<T>><<<(unsigned)grid, kThreads, 0, stream>>>(
       sink, n, 0u, nvec, seed, offset, round_keys(seed), lim, red);
   if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
+  return ZIG_OK;
+}
+
+static_assert(sizeof(zig_request) == 56, "zig_request layout");
+
+size_t batch_ws_bytes(uint32_t count) { return batch_workspace_total(count); }
+
+int batch_occupancy(int dev) {
+  static std::atomic<int> cache[kMaxDevices];
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kThreads, 0) !=
+          cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  cache[dev].store(occ, std::memory_order_relaxed);
+  return occ;
+}
+
+zig_status check_request(const zig_request& q) {
+  if (q.dist != ZIG_EXP && q.dist != ZIG_NORMAL) return ZIG_E_INVAL;
+  if (q.dtype != ZIG_F32 && q.dtype != ZIG_F64) return ZIG_E_INVAL;
+  if (q.n >= (1ull << kBatchPosBits)) return ZIG_E_RANGE;
+  if (q.n > 0 && q.out == nullptr) return ZIG_E_INVAL;
+  if ((uintptr_t)q.out % (q.dtype == ZIG_F64 ? 8 : 4)) return ZIG_E_ALIGN;
+  if (q.n > 0 && q.n - 1 > UINT64_MAX - q.offset) return ZIG_E_RANGE;
+  if (q.dist == ZIG_EXP && !(q.p0 > 0.0 && std::isfinite(q.p0))) return ZIG_E_INVAL;
+  if (q.dist == ZIG_NORMAL && !(q.p1 > 0.0 && std::isfinite(q.p1) && std::isfinite(q.p0)))
+    return ZIG_E_INVAL;
   return ZIG_OK;
 }
 
@@ -929,6 +1014,44 @@ zig_status zig_moments_noalloc(zig_dist dist, zig_dtype dtype, uint64_t n, uint6
                      g_dev[dev].d_static_scratch, kStaticScratchBytes, stream);
 }
 
+size_t zig_batch_workspace_bytes(uint32_t count) { return batch_ws_bytes(count); }
+
+zig_status zig_batch_validate(const zig_request* h_reqs, uint32_t count) {
+  if (count > 0 && h_reqs == nullptr) return ZIG_E_INVAL;
+  if (count >= (1u << kBatchReqBits)) return ZIG_E_RANGE;
+  for (uint32_t r = 0; r < count; ++r) {
+    const zig_status st = check_request(h_reqs[r]);
+    if (st != ZIG_OK) return st;
+  }
+  return ZIG_OK;
+}
+
+zig_status zig_batch(const zig_request* d_reqs, uint32_t count, unsigned long long* d_done_ns,
+                     void* d_workspace, size_t workspace_bytes, void* stream) {
+  if (count == 0) return ZIG_OK;
+  if (d_reqs == nullptr || d_workspace == nullptr) return ZIG_E_INVAL;
+  if (count >= (1u << kBatchReqBits)) return ZIG_E_RANGE;
+  if ((uintptr_t)d_workspace % 16 || (uintptr_t)d_reqs % 8 || (uintptr_t)d_done_ns % 8)
+    return ZIG_E_ALIGN;
+  if (workspace_bytes < batch_ws_bytes(count)) return ZIG_E_NOMEM;
+  int dev;
+  zig_status st = current_device(&dev);
+  if (st != ZIG_OK) return st;
+  if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
+  cudaStream_t s = (cudaStream_t)stream;
+  BatchHeader* hdr = (BatchHeader*)d_workspace;
+  BatchReq* reqs = (BatchReq*)((char*)d_workspace + batch_header_bytes());
+  const uint32_t nranges = (uint32_t)(g_dev[dev].sms < kBatchMaxRanges ? g_dev[dev].sms
+                                                                       : kBatchMaxRanges);
+  batch_prep_kernel<<<1, 1024, 0, s>>>(d_reqs, count, reqs, hdr, d_done_ns, nranges);
+  if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
+  const unsigned grid = (unsigned)(g_dev[dev].sms * batch_occupancy(dev));
+  Limits lim{g_max_att.load(), g_max_tail.load()};
+  batch_kernel<<<grid, kThreads, 0, s>>>(reqs, hdr, lim);
+  if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
+  return ZIG_OK;
+}
+
 zig_status zig_status_poll(void* stream) {
   int dev;
   zig_status st = current_device(&dev);
@@ -943,6 +1066,7 @@ zig_status zig_status_poll(void* stream) {
     return ZIG_E_CUDA;
   }
   if (h & kWaitBit) return ZIG_E_TIMEOUT;
+  if (h & kBatchInvalidBit) return ZIG_E_INVAL;
   if (h & kLoopLimitBit) return ZIG_E_LOOP_LIMIT;
   return ZIG_OK;
 }
