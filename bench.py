@@ -42,6 +42,8 @@ def parse_args():
     p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
     p.add_argument("--n", type=int, default=None,
                    help="override the per-step size (for small profiling captures)")
+    p.add_argument("--no-tune", action="store_true",
+                   help="skip the launch-shape autotuner (use the default shape)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the CPU baseline, e2e, variant and batch measurements")
     return p.parse_args()
@@ -210,6 +212,11 @@ def run_zig(args):
     def counter(step):  # fresh counters per step and rank (weak scaling)
         return c["offset"] + (step * world + rank) * n
 
+    tuned = None
+    if not args.no_tune:
+        # pick the launch shape on the workload's own output buffer (> L2)
+        chosen, results = z.zig_autotune(c["dist"], c["dtype"], out, reps=3, stream=stream)
+        tuned = {"chosen": chosen, "measured": results}
     for k in range(args.warmup):
         fn(out, n, W.SEED, counter(k), stream=stream)
     torch.cuda.synchronize()
@@ -253,7 +260,10 @@ def run_zig(args):
                      "kernel": "gen_kernel<normal,double>",
                      "algorithmic_bytes_per_launch": n * esize},
         "device_status": z.zig_strerror(status),
+        "launch_shape": z.zig_tune_get(c["dist"], c["dtype"]),
     }
+    if tuned is not None:
+        line["autotune"] = tuned
     if not args.no_extras:
         line["e2e"] = measure_e2e(z, fn, out, n, esize, counter, stream, args)
     if rank == 0 and world == 1 and not args.no_extras:
@@ -312,6 +322,7 @@ def measure_variants(z, stream, steps: int = 100):
         es = 8 if dtype == W.F64 else 4
         buf = torch.empty(n, dtype=tdt, device="cuda")
         fn = z.zig_normal if dist == W.NORMAL else z.zig_exponential
+        chosen, _ = z.zig_autotune(dist, dtype, buf, reps=3, stream=stream)
         for k in range(5):
             fn(buf, n, W.SEED, k * n, stream=stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -322,7 +333,7 @@ def measure_variants(z, stream, steps: int = 100):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         res[name] = {"gsamples_s": n / (ms / 1e3) / 1e9, "gb_s": n * es / (ms / 1e3) / 1e9,
-                     "ms_per_launch": ms}
+                     "ms_per_launch": ms, "launch_shape": chosen}
         del buf
     return res
 

@@ -271,6 +271,72 @@ zig_status zig_status_poll(void* stream);
  */
 zig_status zig_set_fringe_limits(int max_attempts, int max_tail);
 
+/*
+ * Launch-shape autotuning.  The paper tunes its CPU code by hand and has
+ * no counterpart; the shapes below change only how the work is spread over
+ * the GPU, never the outputs (element t is always the variate of counter
+ * offset + t).  A shape is V-element vector stores, R vectors per producer
+ * thread and tile (V * R outputs per thread and tile), a register budget
+ * compiled for min_blocks CTAs per SM, and the CTAs per SM actually
+ * launched (blocks_per_sm, 0 = as many as fit).
+ */
+typedef struct zig_tune_entry {
+  int32_t V;
+  int32_t R;
+  int32_t min_blocks;
+  int32_t blocks_per_sm;
+  double gsamples_s; /* measured rate of the shape, Gsamples/s (0 if unmeasured) */
+} zig_tune_entry;
+
+/* The compiled candidate shapes for dtype (blocks_per_sm 0); the first is
+ * the default.  Writes up to max entries to out (host) and returns how
+ * many candidates exist. */
+int zig_tune_candidates(zig_dtype dtype, zig_tune_entry* out, int max);
+
+/*
+ * zig_autotune -- time every candidate shape of zig_exponential (dist
+ * ZIG_EXP) or zig_normal (ZIG_NORMAL) at dtype, each at its full and
+ * reduced CTAs per SM, on the caller's device scratch d_scratch of
+ * scratch_bytes (overwritten; at least 2^20 elements, and larger than the
+ * GPU's L2 cache for a write-bound measurement), reps timed launches each
+ * after one warm-up, with CUDA events on stream, which it synchronises.
+ * Selects the fastest shape for later calls of that (dist, dtype) on this
+ * device and records it for zig_tune_save.  Writes up to max_results
+ * measured entries to results (host, nullable) and the choice to chosen
+ * (host, nullable); *n_results (nullable) receives the number measured.
+ * Returns ZIG_OK, ZIG_E_INVAL, ZIG_E_NOTINIT or ZIG_E_CUDA.  Not for use
+ * during stream capture.
+ */
+zig_status zig_autotune(zig_dist dist, zig_dtype dtype, void* d_scratch, size_t scratch_bytes,
+                        int reps, void* stream, zig_tune_entry* results, int max_results,
+                        int* n_results, zig_tune_entry* chosen);
+
+/* The shape used for (dist, dtype) on the current device (gsamples_s as
+ * measured or loaded, else 0).  ZIG_OK, ZIG_E_INVAL or ZIG_E_CUDA. */
+zig_status zig_tune_get(zig_dist dist, zig_dtype dtype, zig_tune_entry* out);
+
+/* Use shape e (V, R, min_blocks of a candidate; blocks_per_sm >= 0) for
+ * (dist, dtype) on the current device.  ZIG_E_INVAL if e is no candidate. */
+zig_status zig_tune_set(zig_dist dist, zig_dtype dtype, const zig_tune_entry* e);
+
+/*
+ * Tuning cache, one JSON object per line:
+ *   {"device": "<CUDA device name>", "sms": 152, "dist": "normal",
+ *    "dtype": "f64", "V": 4, "R": 4, "min_blocks": 4, "blocks_per_sm": 4,
+ *    "gsamples_s": 318.2}
+ * zig_tune_save writes every entry this process measured or loaded (later
+ * entries replace earlier ones with the same device, SM count, dist and
+ * dtype).  zig_tune_load reads a file; entries whose device name and SM
+ * count match a device take effect on it (now if its tables are built,
+ * else at zig_build_tables).  zig_build_tables loads the file named by the
+ * environment variable ZIG_TUNE_CACHE, if set, once per process.  Lines
+ * that do not parse, or name no candidate shape, are skipped.  ZIG_OK,
+ * ZIG_E_INVAL (null path; for load, an unreadable file) or ZIG_E_CUDA
+ * (save: the file cannot be written).
+ */
+zig_status zig_tune_save(const char* path);
+zig_status zig_tune_load(const char* path);
+
 #ifdef __cplusplus
 }
 #endif

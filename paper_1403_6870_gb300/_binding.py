@@ -75,6 +75,21 @@ _moments_noalloc = _sig("zig_moments_noalloc", _int, [_int, _int, _u64, _u64, _u
 _set_limits = _sig("zig_set_fringe_limits", _int, [_int, _int])
 
 
+class zig_tune_entry(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_int32), ("R", ctypes.c_int32), ("min_blocks", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("gsamples_s", ctypes.c_double)]
+
+
+_TuneP = ctypes.POINTER(zig_tune_entry)
+_tune_candidates = _sig("zig_tune_candidates", _int, [_int, _TuneP, _int])
+_autotune = _sig("zig_autotune", _int, [_int, _int, _vp, ctypes.c_size_t, _int, _vp, _TuneP, _int,
+                                        ctypes.POINTER(_int), _TuneP])
+_tune_get = _sig("zig_tune_get", _int, [_int, _int, _TuneP])
+_tune_set = _sig("zig_tune_set", _int, [_int, _int, _TuneP])
+_tune_save = _sig("zig_tune_save", _int, [ctypes.c_char_p])
+_tune_load = _sig("zig_tune_load", _int, [ctypes.c_char_p])
+
+
 def zig_strerror(status: int) -> str:
     return _strerror(int(status)).decode()
 
@@ -232,6 +247,51 @@ def zig_status_poll(stream=None) -> int:
 
 def zig_set_fringe_limits(max_attempts: int = 64, max_tail: int = 16) -> None:
     _check(_set_limits(int(max_attempts), int(max_tail)), "zig_set_fringe_limits")
+
+
+def _entry_dict(e: zig_tune_entry) -> dict:
+    return {"V": e.V, "R": e.R, "min_blocks": e.min_blocks, "blocks_per_sm": e.blocks_per_sm,
+            "gsamples_s": e.gsamples_s}
+
+
+def zig_tune_candidates(dtype: int) -> list:
+    """Compiled candidate shapes for dtype (the first is the default)."""
+    buf = (zig_tune_entry * 64)()
+    k = int(_tune_candidates(int(dtype), buf, 64))
+    return [_entry_dict(buf[i]) for i in range(min(k, 64))]
+
+
+def zig_autotune(dist: int, dtype: int, scratch, reps: int = 3, stream=None):
+    """Time every candidate shape on the device tensor `scratch` and select
+    the fastest for (dist, dtype); returns (chosen, all measured) dicts."""
+    buf = (zig_tune_entry * 64)()
+    n = _int(0)
+    chosen = zig_tune_entry()
+    nbytes = scratch.numel() * scratch.element_size()
+    _check(_autotune(int(dist), int(dtype), scratch.data_ptr(), nbytes, int(reps),
+                     _stream_handle(stream, scratch), buf, 64, ctypes.byref(n),
+                     ctypes.byref(chosen)), "zig_autotune")
+    return _entry_dict(chosen), [_entry_dict(buf[i]) for i in range(min(n.value, 64))]
+
+
+def zig_tune_get(dist: int, dtype: int) -> dict:
+    e = zig_tune_entry()
+    _check(_tune_get(int(dist), int(dtype), ctypes.byref(e)), "zig_tune_get")
+    return _entry_dict(e)
+
+
+def zig_tune_set(dist: int, dtype: int, entry: dict) -> None:
+    e = zig_tune_entry(int(entry["V"]), int(entry["R"]), int(entry["min_blocks"]),
+                       int(entry.get("blocks_per_sm", 0)), float(entry.get("gsamples_s", 0.0)))
+    _check(_tune_set(int(dist), int(dtype), ctypes.byref(e)), "zig_tune_set")
+
+
+def zig_tune_save(path: str) -> None:
+    _check(_tune_save(os.fsencode(path)), "zig_tune_save")
+
+
+def zig_tune_load(path: str) -> None:
+    _check(_tune_load(os.fsencode(path)), "zig_tune_load")
 
 
 def raw_call(name: str, *args) -> int:  # noqa: C901

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["zig_gen.cu"]
 CU_HEADERS = ["zig_device.cuh", "zig_batch.cuh"]
-CPP_SOURCES = ["zig_tables.cpp"]
+CPP_SOURCES = ["zig_tables.cpp", "zig_tune.cpp"]
 
 
 def _nvcc() -> str:

@@ -27,6 +27,8 @@
 #include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -97,16 +99,23 @@ constexpr unsigned long long kWaitLimitNs = 20ull * 1000ull * 1000ull * 1000ull;
 constexpr unsigned kWaitBit = 1u << 9;          // status bit: a wait gave up
 
 // V elements per vector store, R vector stores per producer thread per tile.
+// A generation shape: V-element vectors (one vector store each), R vectors
+// per producer thread and tile (S = V R outputs per thread and tile), and
+// the CTAs per SM the register budget is compiled for.  The outputs do not
+// depend on the shape: element t is always the variate of counter
+// offset + t.
+template <int V_, int R_, int MB_>
+struct Shape {
+  static constexpr int V = V_, R = R_, MB = MB_;
+};
+
+// Default shapes (the batch and fused kernels use these).
 template <typename T>
 struct GenShape;
 template <>
-struct GenShape<double> {
-  static constexpr int V = ZIG_GEN_V64, R = ZIG_GEN_R64;
-};
+struct GenShape<double> : Shape<ZIG_GEN_V64, ZIG_GEN_R64, ZIG_GEN_MINBLOCKS> {};
 template <>
-struct GenShape<float> {
-  static constexpr int V = ZIG_GEN_V32, R = ZIG_GEN_R32;
-};
+struct GenShape<float> : Shape<ZIG_GEN_V32, ZIG_GEN_R32, ZIG_GEN_MINBLOCKS> {};
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -457,11 +466,11 @@ constexpr int kUnrollR = ZIG_GEN_UNROLL_R;
 // NOWRAP: the low counter words do not wrap inside the run.  full: every
 // vector lies inside the output (else vector r exists only if
 // v0 + r kPThreads < nvec).
-template <int DIST, typename T, bool NOWRAP, typename Sink>
+template <int DIST, typename T, typename Shp, bool NOWRAP, typename Sink>
 __device__ __forceinline__ unsigned producer_tile(Sink& sink, uint64_t g0, uint64_t v0,
                                                   uint64_t nvec, bool full, const RoundKeys& rk,
                                                   const T* sX, uint32_t L) {
-  constexpr int V = GenShape<T>::V, R = GenShape<T>::R;
+  constexpr int V = Shp::V, R = Shp::R;
   unsigned fm = 0;
   const RunState run(g0, rk);
 #pragma unroll kUnrollR
@@ -513,13 +522,13 @@ struct ReduceOut {
 // returns once every published item has its final value, with sh.done
 // reset to zero and its ring cursor hd advanced past the items.  Returns
 // false if a bounded wait gave up.
-template <int DIST, typename T, typename Sink, typename State>
+template <int DIST, typename T, typename Shp, typename Sink, typename State>
 __device__ __forceinline__ bool gen_tiles(State& sh, Sink& sink, const T* sX, uint64_t n,
                                           uint64_t head, uint64_t nvec, uint64_t seed,
                                           uint64_t offset, const RoundKeys& rk, Limits lim,
                                           uint64_t tile, uint64_t tile_end, uint64_t step,
                                           bool ends, unsigned& hd) {
-  constexpr int V = GenShape<T>::V, R = GenShape<T>::R, S = V * R;
+  constexpr int V = Shp::V, R = Shp::R, S = V * R;
   constexpr int kTile = kPThreads * R;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -545,9 +554,9 @@ __device__ __forceinline__ bool gen_tiles(State& sh, Sink& sink, const T* sX, ui
       const bool full = (tile + 1) * kTile <= nvec;
       unsigned fm;  // outputs of this thread whose layer index is >= L_max
       if ((uint32_t)g0 <= 0xFFFFFFFFu - kSpan)
-        fm = producer_tile<DIST, T, true>(sink, g0, v0, nvec, full, rk, sX, L);
+        fm = producer_tile<DIST, T, Shp, true>(sink, g0, v0, nvec, full, rk, sX, L);
       else
-        fm = producer_tile<DIST, T, false>(sink, g0, v0, nvec, full, rk, sX, L);
+        fm = producer_tile<DIST, T, Shp, false>(sink, g0, v0, nvec, full, rk, sX, L);
       if (__any_sync(0xFFFFFFFFu, fm != 0)) {
         const unsigned fmask = fm;
         ok = publish(sh, __popc(fmask), [&](int k) {
@@ -615,11 +624,11 @@ __device__ __forceinline__ bool gen_tiles(State& sh, Sink& sink, const T* sX, ui
 
 // One launch covers outputs [0, n) (layout as in gen_tiles); CTA b takes
 // tiles b, b + gridDim.x, ... and CTA 0 the head and tail elements.
-template <int DIST, typename T, typename Sink>
-__global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
+template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>>
+__global__ void __launch_bounds__(kThreads, Shp::MB)
     gen_kernel(Sink sink, uint64_t n, uint32_t head, uint64_t nvec, uint64_t seed,
                uint64_t offset, const RoundKeys rk, Limits lim, ReduceOut red) {
-  constexpr int R = GenShape<T>::R;
+  constexpr int R = Shp::R;
   constexpr int kTile = kPThreads * R;
   __shared__ CtaState<T> sh;
   __shared__ unsigned shist[Sink::kReduce ? kBins : 1];
@@ -639,8 +648,8 @@ __global__ void __launch_bounds__(kThreads, ZIG_GEN_MINBLOCKS)
 
   const uint64_t ntiles = (nvec + kTile - 1) / kTile;
   unsigned hd = 0;
-  gen_tiles<DIST, T>(sh, sink, sh.sX, n, head, nvec, seed, offset, rk, lim, blockIdx.x, ntiles,
-                     gridDim.x, blockIdx.x == 0, hd);
+  gen_tiles<DIST, T, Shp>(sh, sink, sh.sX, n, head, nvec, seed, offset, rk, lim, blockIdx.x,
+                          ntiles, gridDim.x, blockIdx.x == 0, hd);
 
   if constexpr (Sink::kReduce) {
     // CTA partials in thread order, then the CTA's histogram into the
@@ -693,11 +702,21 @@ std::atomic<bool> g_host_ready{false};
 std::atomic<int> g_max_att{64};
 std::atomic<int> g_max_tail{16};
 
+// Launch shape in use for one (dist, dtype): candidate index, CTAs per SM
+// (0 = as many as fit) and the rate it was measured at.
+struct Selection {
+  std::atomic<int> variant{0};
+  std::atomic<int> bps{0};
+  std::atomic<double> rate{0.0};
+};
+
 struct DeviceState {
   std::atomic<bool> ready{false};
   unsigned int* d_status = nullptr;
   void* d_static_scratch = nullptr;  // device address of g_moment_scratch
   int sms = 0;
+  char name[256] = {0};
+  Selection sel[2][2];  // [dist][dtype]
 };
 DeviceState g_dev[kMaxDevices];
 
@@ -759,14 +778,14 @@ RoundKeys round_keys(uint64_t seed) {
   return rk;
 }
 
-template <int DIST, typename T, typename Sink>
+template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>>
 int occupancy_blocks(int dev) {
   static std::atomic<int> cache[kMaxDevices];
   int v = cache[dev].load(std::memory_order_relaxed);
   if (v > 0) return v;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gen_kernel<DIST, T, Sink>, kThreads,
-                                                    0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gen_kernel<DIST, T, Sink, Shp>,
+                                                    kThreads, 0) != cudaSuccess ||
       occ < 1) {
     cudaGetLastError();
     occ = 1;
@@ -775,25 +794,73 @@ int occupancy_blocks(int dev) {
   return occ;
 }
 
-template <int DIST, typename T>
+// Materialising launch of shape Shp with at most bps CTAs per SM (0: as
+// many as fit).
+template <int DIST, typename T, typename Shp>
 zig_status launch_gen(void* out, uint64_t n, uint64_t seed, uint64_t offset,
-                      cudaStream_t stream, int dev) {
-  constexpr int V = GenShape<T>::V, R = GenShape<T>::R;
+                      cudaStream_t stream, int dev, int bps) {
+  constexpr int V = Shp::V, R = Shp::R;
   const uintptr_t addr = (uintptr_t)out;
   const uint64_t align_elems = (uint64_t)((V - (addr / sizeof(T)) % V) % V);
   const uint64_t head = align_elems < n ? align_elems : n;
   const uint64_t nvec = (n - head) / V;
   const uint64_t tiles = (nvec + (uint64_t)kPThreads * R - 1) / ((uint64_t)kPThreads * R);
-  const uint64_t cap =
-      (uint64_t)g_dev[dev].sms * (uint64_t)occupancy_blocks<DIST, T, StoreSink<T>>(dev);
+  int occ = occupancy_blocks<DIST, T, StoreSink<T>, Shp>(dev);
+  if (bps > 0 && bps < occ) occ = bps;
+  const uint64_t cap = (uint64_t)g_dev[dev].sms * (uint64_t)occ;
   uint64_t grid = tiles < cap ? tiles : cap;
   if (grid < 1) grid = 1;
   Limits lim{g_max_att.load(), g_max_tail.load()};
   StoreSink<T> sink{(T*)out, head};
-  gen_kernel<DIST, T, StoreSink<T>><<<(unsigned)grid, kThreads, 0, stream>>>(
+  gen_kernel<DIST, T, StoreSink<T>, Shp><<<(unsigned)grid, kThreads, 0, stream>>>(
       sink, n, (uint32_t)head, nvec, seed, offset, round_keys(seed), lim, ReduceOut{});
   if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
   return ZIG_OK;
+}
+
+// The autotuner's candidate shapes per precision (index 0 is the default).
+// FP64: 16- or 32-byte vectors, 8-32 outputs per thread and tile, 3-4
+// CTAs per SM; FP32 likewise with 16- or 32-byte vectors.
+constexpr int kVariants = 5;
+template <typename T>
+struct Variants;
+template <>
+struct Variants<double> {
+  static constexpr int V[kVariants] = {GenShape<double>::V, 4, 2, 4, 2};
+  static constexpr int R[kVariants] = {GenShape<double>::R, 2, 4, 4, 8};
+  static constexpr int MB[kVariants] = {GenShape<double>::MB, 4, 4, 3, 4};
+};
+template <>
+struct Variants<float> {
+  static constexpr int V[kVariants] = {GenShape<float>::V, 8, 4, 8, 4};
+  static constexpr int R[kVariants] = {GenShape<float>::R, 1, 4, 2, 2};
+  static constexpr int MB[kVariants] = {GenShape<float>::MB, 4, 4, 3, 4};
+};
+
+template <int DIST, typename T, int K>
+using VariantShape = Shape<Variants<T>::V[K], Variants<T>::R[K], Variants<T>::MB[K]>;
+
+template <int DIST, typename T>
+zig_status launch_variant(int k, void* out, uint64_t n, uint64_t seed, uint64_t offset,
+                          cudaStream_t stream, int dev, int bps) {
+  switch (k) {
+    case 1: return launch_gen<DIST, T, VariantShape<DIST, T, 1>>(out, n, seed, offset, stream, dev, bps);
+    case 2: return launch_gen<DIST, T, VariantShape<DIST, T, 2>>(out, n, seed, offset, stream, dev, bps);
+    case 3: return launch_gen<DIST, T, VariantShape<DIST, T, 3>>(out, n, seed, offset, stream, dev, bps);
+    case 4: return launch_gen<DIST, T, VariantShape<DIST, T, 4>>(out, n, seed, offset, stream, dev, bps);
+    default: return launch_gen<DIST, T, GenShape<T>>(out, n, seed, offset, stream, dev, bps);
+  }
+}
+
+template <int DIST, typename T>
+int variant_occupancy(int k, int dev) {
+  switch (k) {
+    case 1: return occupancy_blocks<DIST, T, StoreSink<T>, VariantShape<DIST, T, 1>>(dev);
+    case 2: return occupancy_blocks<DIST, T, StoreSink<T>, VariantShape<DIST, T, 2>>(dev);
+    case 3: return occupancy_blocks<DIST, T, StoreSink<T>, VariantShape<DIST, T, 3>>(dev);
+    case 4: return occupancy_blocks<DIST, T, StoreSink<T>, VariantShape<DIST, T, 4>>(dev);
+    default: return occupancy_blocks<DIST, T, StoreSink<T>, GenShape<T>>(dev);
+  }
 }
 
 // Grid of the fused reduction on device dev (one partial per CTA).
@@ -822,7 +889,7 @@ zig_status launch_moments(uint64_t n, uint64_t seed, uint64_t offset, double* d_
   }
   Limits lim{g_max_att.load(), g_max_tail.load()};
   ReduceOut red{d_sums, d_hist, (double*)((char*)d_ws + kTicketBytes), (unsigned*)d_ws};
-  MomentSink<T> sink;
+  MomentSink<T> sink{};
   gen_kernel<DIST, T, MomentSink<T>><<<(unsigned)grid, kThreads, 0, stream>>>(
       sink, n, 0u, nvec, seed, offset, round_keys(seed), lim, red);
   if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
@@ -861,6 +928,42 @@ zig_status check_request(const zig_request& q) {
   return ZIG_OK;
 }
 
+template <typename T>
+int variant_index(const zig_tune_entry& e) {
+  for (int k = 0; k < kVariants; ++k)
+    if (Variants<T>::V[k] == e.V && Variants<T>::R[k] == e.R && Variants<T>::MB[k] == e.min_blocks)
+      return k;
+  return -1;
+}
+
+int variant_index(int dtype, const zig_tune_entry& e) {
+  return dtype == ZIG_F64 ? variant_index<double>(e) : variant_index<float>(e);
+}
+
+template <typename T>
+zig_tune_entry variant_entry(int k, int bps, double rate) {
+  return zig_tune_entry{Variants<T>::V[k], Variants<T>::R[k], Variants<T>::MB[k], bps, rate};
+}
+
+zig_tune_entry variant_entry(int dtype, int k, int bps, double rate) {
+  return dtype == ZIG_F64 ? variant_entry<double>(k, bps, rate) : variant_entry<float>(k, bps, rate);
+}
+
+// Cached choices for device dev (its name and SM count) take effect.
+void apply_cached(int dev) {
+  for (int d = 0; d < 2; ++d)
+    for (int t = 0; t < 2; ++t) {
+      zig_tune_entry e;
+      if (!tune_cache_get(g_dev[dev].name, g_dev[dev].sms, d, t, &e)) continue;
+      const int k = variant_index(t, e);
+      if (k < 0 || e.blocks_per_sm < 0) continue;
+      Selection& sel = g_dev[dev].sel[d][t];
+      sel.variant.store(k);
+      sel.bps.store(e.blocks_per_sm);
+      sel.rate.store(e.gsamples_s);
+    }
+}
+
 zig_status generate(int dist, void* out, uint64_t n, uint64_t seed, uint64_t offset,
                     zig_dtype dtype, void* stream) {
   if (dtype != ZIG_F32 && dtype != ZIG_F64) return ZIG_E_INVAL;
@@ -875,11 +978,22 @@ zig_status generate(int dist, void* out, uint64_t n, uint64_t seed, uint64_t off
   if (st != ZIG_OK) return st;
   if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
   cudaStream_t s = (cudaStream_t)stream;
+  const Selection& sel = g_dev[dev].sel[dist == ZIG_EXP ? 0 : 1][dtype == ZIG_F64 ? 1 : 0];
+  const int k = sel.variant.load(std::memory_order_relaxed);
+  const int bps = sel.bps.load(std::memory_order_relaxed);
   if (dist == ZIG_EXP)
-    return dtype == ZIG_F64 ? launch_gen<ZIG_EXP, double>(out, n, seed, offset, s, dev)
-                            : launch_gen<ZIG_EXP, float>(out, n, seed, offset, s, dev);
-  return dtype == ZIG_F64 ? launch_gen<ZIG_NORMAL, double>(out, n, seed, offset, s, dev)
-                          : launch_gen<ZIG_NORMAL, float>(out, n, seed, offset, s, dev);
+    return dtype == ZIG_F64 ? launch_variant<ZIG_EXP, double>(k, out, n, seed, offset, s, dev, bps)
+                            : launch_variant<ZIG_EXP, float>(k, out, n, seed, offset, s, dev, bps);
+  return dtype == ZIG_F64 ? launch_variant<ZIG_NORMAL, double>(k, out, n, seed, offset, s, dev, bps)
+                          : launch_variant<ZIG_NORMAL, float>(k, out, n, seed, offset, s, dev, bps);
+}
+
+int variant_occupancy_any(int dist, int dtype, int k, int dev) {
+  if (dist == ZIG_EXP)
+    return dtype == ZIG_F64 ? variant_occupancy<ZIG_EXP, double>(k, dev)
+                            : variant_occupancy<ZIG_EXP, float>(k, dev);
+  return dtype == ZIG_F64 ? variant_occupancy<ZIG_NORMAL, double>(k, dev)
+                          : variant_occupancy<ZIG_NORMAL, float>(k, dev);
 }
 
 }  // namespace
@@ -887,6 +1001,13 @@ zig_status generate(int dist, void* out, uint64_t n, uint64_t seed, uint64_t off
 const zig_tables_export* host_tables(int dist) {
   if (ensure_host_tables() != ZIG_OK) return nullptr;
   return &g_host[dist];
+}
+
+bool tune_shape_known(int dtype, const zig_tune_entry& e) { return variant_index(dtype, e) >= 0; }
+
+void tune_apply_loaded() {
+  for (int dev = 0; dev < kMaxDevices; ++dev)
+    if (g_dev[dev].ready.load(std::memory_order_acquire)) apply_cached(dev);
 }
 
 }  // namespace zig
@@ -935,10 +1056,127 @@ zig_status zig_build_tables(void) {
     cudaGetLastError();
     return ZIG_E_CUDA;
   }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return ZIG_E_CUDA;
+  }
   g_dev[dev].d_status = (unsigned int*)status;
   g_dev[dev].d_static_scratch = scratch;
   g_dev[dev].sms = sms;
+  std::snprintf(g_dev[dev].name, sizeof(g_dev[dev].name), "%s", prop.name);
+  static std::once_flag env_cache;
+  std::call_once(env_cache, [] {
+    const char* path = std::getenv("ZIG_TUNE_CACHE");
+    if (path && *path) tune_cache_load(path);
+  });
+  apply_cached(dev);
   g_dev[dev].ready.store(true, std::memory_order_release);
+  return ZIG_OK;
+}
+
+int zig_tune_candidates(zig_dtype dtype, zig_tune_entry* out, int max) {
+  if (dtype != ZIG_F32 && dtype != ZIG_F64) return 0;
+  for (int k = 0; k < kVariants && out && k < max; ++k) out[k] = variant_entry(dtype, k, 0, 0.0);
+  return kVariants;
+}
+
+zig_status zig_tune_get(zig_dist dist, zig_dtype dtype, zig_tune_entry* out) {
+  if ((dist != ZIG_EXP && dist != ZIG_NORMAL) || (dtype != ZIG_F32 && dtype != ZIG_F64) || !out)
+    return ZIG_E_INVAL;
+  int dev;
+  const zig_status st = current_device(&dev);
+  if (st != ZIG_OK) return st;
+  const Selection& sel = g_dev[dev].sel[dist][dtype];
+  *out = variant_entry(dtype, sel.variant.load(), sel.bps.load(), sel.rate.load());
+  return ZIG_OK;
+}
+
+zig_status zig_tune_set(zig_dist dist, zig_dtype dtype, const zig_tune_entry* e) {
+  if ((dist != ZIG_EXP && dist != ZIG_NORMAL) || (dtype != ZIG_F32 && dtype != ZIG_F64) || !e)
+    return ZIG_E_INVAL;
+  const int k = variant_index(dtype, *e);
+  if (k < 0 || e->blocks_per_sm < 0 || e->blocks_per_sm > 64) return ZIG_E_INVAL;
+  int dev;
+  const zig_status st = current_device(&dev);
+  if (st != ZIG_OK) return st;
+  Selection& sel = g_dev[dev].sel[dist][dtype];
+  sel.variant.store(k);
+  sel.bps.store(e->blocks_per_sm);
+  sel.rate.store(e->gsamples_s);
+  return ZIG_OK;
+}
+
+zig_status zig_autotune(zig_dist dist, zig_dtype dtype, void* d_scratch, size_t scratch_bytes,
+                        int reps, void* stream, zig_tune_entry* results, int max_results,
+                        int* n_results, zig_tune_entry* chosen) {
+  if ((dist != ZIG_EXP && dist != ZIG_NORMAL) || (dtype != ZIG_F32 && dtype != ZIG_F64) ||
+      d_scratch == nullptr || reps < 1 || reps > 1000)
+    return ZIG_E_INVAL;
+  const size_t es = dtype == ZIG_F64 ? 8 : 4;
+  const uint64_t n = scratch_bytes / es;
+  if (n < (1ull << 20) || (uintptr_t)d_scratch % es) return ZIG_E_INVAL;
+  int dev;
+  zig_status st = current_device(&dev);
+  if (st != ZIG_OK) return st;
+  if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return ZIG_E_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ZIG_E_CUDA;
+  }
+  int count = 0;
+  int best_k = 0, best_b = 0;
+  double best = -1.0;
+  st = ZIG_OK;
+  for (int k = 0; k < kVariants && st == ZIG_OK; ++k) {
+    const int occ = variant_occupancy_any(dist, dtype, k, dev);
+    // as many CTAs per SM as fit, and one fewer
+    for (int b = occ; b >= 1 && b >= occ - 1 && st == ZIG_OK; --b) {
+      auto launch = [&] {
+        return dist == ZIG_EXP
+                   ? (dtype == ZIG_F64
+                          ? launch_variant<ZIG_EXP, double>(k, d_scratch, n, 0, 0, s, dev, b)
+                          : launch_variant<ZIG_EXP, float>(k, d_scratch, n, 0, 0, s, dev, b))
+                   : (dtype == ZIG_F64
+                          ? launch_variant<ZIG_NORMAL, double>(k, d_scratch, n, 0, 0, s, dev, b)
+                          : launch_variant<ZIG_NORMAL, float>(k, d_scratch, n, 0, 0, s, dev, b));
+      };
+      st = launch();
+      if (st == ZIG_OK && cudaEventRecord(e0, s) != cudaSuccess) st = ZIG_E_CUDA;
+      for (int i = 0; i < reps && st == ZIG_OK; ++i) st = launch();
+      float ms = 0.0f;
+      if (st == ZIG_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                           cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = ZIG_E_CUDA;
+      if (st != ZIG_OK) break;
+      const double rate = (double)n * reps / ((double)ms * 1e6);
+      if (results && count < max_results) results[count] = variant_entry(dtype, k, b, rate);
+      ++count;
+      if (rate > best) {
+        best = rate;
+        best_k = k;
+        best_b = b;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ZIG_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  Selection& sel = g_dev[dev].sel[dist][dtype];
+  sel.variant.store(best_k);
+  sel.bps.store(best_b);
+  sel.rate.store(best);
+  const zig_tune_entry e = variant_entry(dtype, best_k, best_b, best);
+  tune_cache_put(g_dev[dev].name, g_dev[dev].sms, dist, dtype, e);
+  if (chosen) *chosen = e;
+  if (n_results) *n_results = count;
   return ZIG_OK;
 }
 

@@ -16,6 +16,18 @@ int build_host_tables(zig_tables_export* exp_tab, zig_tables_export* nrm_tab);
 // Host tables, built once per process (zig_gen.cu).
 const zig_tables_export* host_tables(int dist);
 
+// Tuning cache (zig_tune.cpp): chosen shapes keyed by device name, SM
+// count, dist and dtype; JSON Lines load/save return zig_status codes.
+void tune_cache_put(const char* device, int sms, int dist, int dtype, const zig_tune_entry& e);
+bool tune_cache_get(const char* device, int sms, int dist, int dtype, zig_tune_entry* e);
+int tune_cache_load(const char* path);
+int tune_cache_save(const char* path);
+
+// zig_gen.cu: whether (V, R, min_blocks) is a compiled candidate for
+// dtype, and applying cached choices to every device whose tables are built.
+bool tune_shape_known(int dtype, const zig_tune_entry& e);
+void tune_apply_loaded();
+
 }  // namespace zig
 
 #endif

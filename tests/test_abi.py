@@ -98,3 +98,53 @@ def test_no_cpu_fallback(zig):
         pytest.skip("a GPU is present")
     st = zig.raw_call("zig_normal", 0x1000, 1 << 10, 1, 0, zig.ZIG_F64, None)
     assert st in (zig.ZIG_E_CUDA, zig.ZIG_E_NOTINIT)
+
+
+def test_tune_candidates(zig):
+    f64 = zig.zig_tune_candidates(1)
+    f32 = zig.zig_tune_candidates(0)
+    assert len(f64) == 5 and len(f32) == 5
+    # the defaults come first; all shapes distinct; outputs per thread and
+    # tile fit a warp's ring reservation (32 V R <= 2048)
+    assert (f64[0]["V"], f64[0]["R"], f64[0]["min_blocks"]) == (4, 4, 4)
+    assert (f32[0]["V"], f32[0]["R"], f32[0]["min_blocks"]) == (8, 2, 4)
+    for c in (f64, f32):
+        assert len({(e["V"], e["R"], e["min_blocks"]) for e in c}) == len(c)
+        assert all(32 * e["V"] * e["R"] <= 2048 for e in c)
+    assert zig.zig_tune_candidates(7) == []
+
+
+def test_tune_cache_roundtrip(zig, tmp_path):
+    """JSON Lines cache: valid lines load, invalid ones are skipped, a later
+    line replaces an earlier one for the same key, and save writes what was
+    loaded (no device involved: the names are not this machine's GPUs)."""
+    import json
+
+    src = tmp_path / "in.jsonl"
+    lines = [
+        {"device": "test-device-A", "sms": 8, "dist": "normal", "dtype": "f64", "V": 4, "R": 2,
+         "min_blocks": 4, "blocks_per_sm": 3, "gsamples_s": 1.5},
+        {"device": "test-device-A", "sms": 8, "dist": "normal", "dtype": "f64", "V": 2, "R": 4,
+         "min_blocks": 4, "blocks_per_sm": 2, "gsamples_s": 2.5},
+        {"device": "test \"quoted\" B", "sms": 9, "dist": "exp", "dtype": "f32", "V": 8, "R": 1,
+         "min_blocks": 4, "blocks_per_sm": 0, "gsamples_s": 3.0},
+        # no such candidate shape, unknown dist, missing field: skipped
+        {"device": "test-device-A", "sms": 8, "dist": "exp", "dtype": "f64", "V": 3, "R": 3,
+         "min_blocks": 4, "blocks_per_sm": 1},
+        {"device": "test-device-A", "sms": 8, "dist": "gamma", "dtype": "f64", "V": 4, "R": 4,
+         "min_blocks": 4, "blocks_per_sm": 1},
+        {"device": "test-device-A", "sms": 8, "dist": "exp", "dtype": "f64", "V": 4, "R": 4},
+    ]
+    src.write_text("\n".join(json.dumps(x) for x in lines) + "\nnot json at all\n")
+    zig.zig_tune_load(str(src))
+    out = tmp_path / "out.jsonl"
+    zig.zig_tune_save(str(out))
+    got = [json.loads(x) for x in out.read_text().splitlines()]
+    mine = {(g["device"], g["sms"], g["dist"], g["dtype"]): g for g in got
+            if g["device"].startswith("test")}
+    assert set(mine) == {("test-device-A", 8, "normal", "f64"), ('test "quoted" B', 9, "exp", "f32")}
+    a = mine[("test-device-A", 8, "normal", "f64")]
+    assert (a["V"], a["R"], a["min_blocks"], a["blocks_per_sm"]) == (2, 4, 4, 2)
+    assert a["gsamples_s"] == pytest.approx(2.5)
+    with pytest.raises(zig.ZigError):
+        zig.zig_tune_load(str(tmp_path / "missing.jsonl"))
