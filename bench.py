@@ -25,6 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
+from paper_1403_6870_gb300.shard import step_counter  # noqa: E402
 
 METRIC = "Gsamples/s (exp & normal, FP64/FP32) and % HBM-write roofline; batched vs plain"
 UNIT = "Gsamples/s"
@@ -210,7 +211,7 @@ def run_zig(args):
     stream = torch.cuda.current_stream()
 
     def counter(step):  # fresh counters per step and rank (weak scaling)
-        return c["offset"] + (step * world + rank) * n
+        return step_counter(c["offset"], step, rank, world, n)
 
     tuned = None
     if not args.no_tune:
