@@ -30,7 +30,8 @@ from paper_1403_6870_gb300.shard import step_counter  # noqa: E402
 METRIC = "Gsamples/s (exp & normal, FP64/FP32) and % HBM-write roofline; batched vs plain"
 UNIT = "Gsamples/s"
 DEFAULT_WORKLOAD = "normal_f64_2p28"
-KERNEL_SRC = os.path.join(ROOT, "paper_1403_6870_gb300", "csrc", "zig_gen.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1403_6870_gb300", "csrc", f)
+               for f in ("zig_gen.cu", "zig_device.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gen_kernel_normal_f64_traffic.txt")
 
 
@@ -45,6 +46,9 @@ def parse_args():
                    help="override the per-step size (for small profiling captures)")
     p.add_argument("--no-tune", action="store_true",
                    help="skip the launch-shape autotuner (use the default shape)")
+    p.add_argument("--batch-requests", type=int, default=None,
+                   help="time only zig_batch on the first K requests of the serving mix "
+                        "(a small case for profiling) and print its line")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the CPU baseline, e2e, variant and batch measurements")
     return p.parse_args()
@@ -65,8 +69,13 @@ def measured_peak():
 
 
 def kernel_hash() -> str:
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """First 16 hex digits of the SHA-256 of the generation kernel's sources
+    (zig_gen.cu followed by zig_device.cuh)."""
+    h = hashlib.sha256()
+    for path in KERNEL_SRCS:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(n: int):
@@ -403,6 +412,7 @@ def measure_batch(z, stream, reps: int = 10):
             evs[k + 1].record(s)
     torch.cuda.synchronize()
     lat_plain = np.array([evs[0].elapsed_time(e) for e in evs[1:]])
+    ms_stream = float(lat_plain[-1])
     # one large plain launch per class with the class's total count
     del bufs
     torch.cuda.empty_cache()
@@ -425,6 +435,8 @@ def measure_batch(z, stream, reps: int = 10):
                                         "gsamples_s": total / (ms_plain / 1e3) / 1e9,
                                         "p50_ms": float(np.percentile(lat_plain, 50)),
                                         "p99_ms": float(np.percentile(lat_plain, 99))},
+            "plain_per_request_stream": {"ms": ms_stream,
+                                         "gsamples_s": total / (ms_stream / 1e3) / 1e9},
             "plain_large_per_class": {"ms": big_ms, "gsamples_s": total / (big_ms / 1e3) / 1e9},
             "batch_vs_large_plain": (total / (ms_batch / 1e3)) / (total / (big_ms / 1e3)),
             "device_status": z.zig_strerror(st),
@@ -432,9 +444,44 @@ def measure_batch(z, stream, reps: int = 10):
                     "transform); the batch applies each request's transform"}
 
 
+def run_batch_only(args):
+    """zig_batch alone on the first K requests of the serving mix: warm-up
+    calls, then timed calls with CUDA events (a small case for ncu)."""
+    import numpy as np
+    import torch
+
+    import paper_1403_6870_gb300 as z
+
+    z.zig_build_tables()
+    reqs = W.batch_requests()[:args.batch_requests]
+    bufs = []
+    for q in reqs:
+        b = torch.empty(q["n"], dtype=torch.float64 if q["dtype"] else torch.float32, device="cuda")
+        q["out"] = b.data_ptr()
+        bufs.append(b)
+    d_reqs = torch.from_numpy(z.pack_requests(reqs).view(np.uint8)).cuda()
+    ws = torch.empty(z.zig_batch_workspace_bytes(len(reqs)), dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        z.zig_batch(d_reqs, len(reqs), ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        z.zig_batch(d_reqs, len(reqs), ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    total = sum(q["n"] for q in reqs)
+    print(json.dumps({"batch_requests": len(reqs), "variates": total, "ms_per_call": ms,
+                      "gsamples_s": total / (ms / 1e3) / 1e9,
+                      "device_status": z.zig_strerror(z.zig_status_poll())}), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.batch_requests:
+        run_batch_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_zig(args)
