@@ -75,7 +75,8 @@ class Tables(ctypes.Structure):
 
 class Words(ctypes.Structure):
     _fields_ = [
-        ("kind", ctypes.c_int), ("seed", ctypes.c_uint64), ("g", ctypes.c_uint64),
+        ("kind", ctypes.c_int), ("dtype", ctypes.c_int), ("dom", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64), ("g", ctypes.c_uint64),
         ("block", ctypes.c_uint32), ("half", ctypes.c_int), ("r", ctypes.c_uint32 * 4),
         ("script", ctypes.POINTER(ctypes.c_uint64)), ("nscript", ctypes.c_int),
         ("pos", ctypes.c_int), ("overrun", ctypes.c_int), ("used", ctypes.c_int),
@@ -99,6 +100,7 @@ def lib():
             L.orc_build_tables.argtypes = [ctypes.c_int] * 4 + [P(Tables)]
             L.orc_words_philox.argtypes = [P(Words), ctypes.c_uint64, ctypes.c_uint64]
             L.orc_words_script.argtypes = [P(Words), P(ctypes.c_uint64), ctypes.c_int]
+            L.orc_words_packed.argtypes = [P(Words), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
             L.orc_next.argtypes = [P(Words)]
             L.orc_next.restype = ctypes.c_uint64
             L.orc_set_limits.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -117,6 +119,11 @@ def lib():
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_int]
             L.orc_fill.restype = ctypes.c_int64
+            L.orc_fill_keyed.argtypes = [P(Tables), P(Tables), ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            L.orc_fill_keyed.restype = ctypes.c_int64
             L.orc_moments.argtypes = [P(Tables), P(Tables), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -171,8 +178,9 @@ def default_threads() -> int:
 
 def fill(dist: int, dtype: int, seed: int, offset: int, n: int, idx=None,
          want_words: bool = False, want_margin: bool = False, nthreads: int | None = None,
-         te: Tables | None = None, tn: Tables | None = None):
-    """Samples at counters offset + pos (pos = idx[k] or k).
+         te: Tables | None = None, tn: Tables | None = None, keying: int = 0):
+    """Samples at counters offset + pos (pos = idx[k] or k); keying 0 =
+    per-index words, 1 = packed keying (orc_words_packed).
 
     Returns (values, errors, words_or_None, margin_or_None)."""
     te = te or tables(EXP)
@@ -183,8 +191,9 @@ def fill(dist: int, dtype: int, seed: int, offset: int, n: int, idx=None,
     out = np.empty(n, dtype=np.float64 if dtype == F64 else np.float32)
     words = np.empty(n, dtype=np.uint8) if want_words else None
     margin = np.empty(n, dtype=np.float64) if want_margin else None
-    errs = lib().orc_fill(
-        ctypes.byref(te), ctypes.byref(tn), dist, dtype, seed & (2**64 - 1), offset & (2**64 - 1),
+    errs = lib().orc_fill_keyed(
+        ctypes.byref(te), ctypes.byref(tn), dist, dtype, int(keying), seed & (2**64 - 1),
+        offset & (2**64 - 1),
         n, None if idx is None else idx.ctypes.data, out.ctypes.data,
         None if words is None else words.ctypes.data,
         None if margin is None else margin.ctypes.data,
@@ -229,6 +238,13 @@ def philox_words(seed: int, g: int, count: int) -> list:
     """The first `count` words of the word stream of counter g."""
     w = Words()
     lib().orc_words_philox(ctypes.byref(w), seed, g)
+    return [int(lib().orc_next(ctypes.byref(w))) for _ in range(count)]
+
+
+def packed_words(seed: int, g: int, dtype: int, count: int) -> list:
+    """The first `count` words of counter g under packed keying."""
+    w = Words()
+    lib().orc_words_packed(ctypes.byref(w), seed, g, dtype)
     return [int(lib().orc_next(ctypes.byref(w))) for _ in range(count)]
 
 

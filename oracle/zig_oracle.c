@@ -68,6 +68,14 @@ void orc_words_philox(orc_words* w, uint64_t seed, uint64_t g) {
   w->g = g;
 }
 
+void orc_words_packed(orc_words* w, uint64_t seed, uint64_t g, int dtype) {
+  memset(w, 0, sizeof(*w));
+  w->kind = 2;
+  w->dtype = dtype;
+  w->seed = seed;
+  w->g = g;
+}
+
 void orc_words_script(orc_words* w, const uint64_t* script, int n) {
   memset(w, 0, sizeof(*w));
   w->kind = 1;
@@ -84,9 +92,29 @@ uint64_t orc_next(orc_words* w) {
     }
     return w->script[w->pos++];
   }
+  if (w->kind == 2) {
+    uint32_t key[2] = {(uint32_t)w->seed, (uint32_t)(w->seed >> 32)};
+    /* packed keying: the first word from the block shared with the
+     * neighbouring counters, then counter g's private stream (domain 1) */
+    w->kind = 0;
+    w->dom = 1u;
+    uint32_t r[4];
+    if (w->dtype == ORC_F64) {
+      uint64_t h = w->g >> 1;
+      uint32_t ctr[4] = {(uint32_t)h, (uint32_t)(h >> 32), 0u, 0u};
+      orc_philox4x32_10(ctr, key, r);
+      int half = (int)(w->g & 1u);
+      return (uint64_t)r[2 * half] | ((uint64_t)r[2 * half + 1] << 32);
+    }
+    uint64_t h = w->g >> 2;
+    uint32_t ctr[4] = {(uint32_t)h, (uint32_t)(h >> 32), 0u, 0u};
+    orc_philox4x32_10(ctr, key, r);
+    uint32_t lane = r[w->g & 3u];
+    return (uint64_t)(lane & 0x1FFu) | ((uint64_t)(lane >> 9) << 41);
+  }
   if (w->half == 0) {
-    /* Block a = w->block of counter g: (g_lo, g_hi, 0, a), key = seed. */
-    uint32_t ctr[4] = {(uint32_t)w->g, (uint32_t)(w->g >> 32), 0u, w->block};
+    /* Block a = w->block of counter g: (g_lo, g_hi, dom, a), key = seed. */
+    uint32_t ctr[4] = {(uint32_t)w->g, (uint32_t)(w->g >> 32), w->dom, w->block};
     uint32_t key[2] = {(uint32_t)w->seed, (uint32_t)(w->seed >> 32)};
     orc_philox4x32_10(ctr, key, w->r);
     w->half = 1;
@@ -603,6 +631,7 @@ typedef struct {
   void* out;
   uint8_t* words;
   double* margin;
+  int keying; /* 0 = per index, 1 = packed */
   int64_t errs;
   /* moments */
   int moments;
@@ -612,7 +641,10 @@ typedef struct {
 
 static double sample_one(const fill_job* jb, uint64_t pos, orc_diag* d) {
   orc_words w;
-  orc_words_philox(&w, jb->seed, jb->offset + pos);
+  if (jb->keying == 1)
+    orc_words_packed(&w, jb->seed, jb->offset + pos, jb->dtype);
+  else
+    orc_words_philox(&w, jb->seed, jb->offset + pos);
   if (jb->dtype == ORC_F64) {
     return jb->dist == ORC_EXP ? orc_exp64(jb->te, &w, d)
                                : orc_normal64(jb->te, jb->tn, &w, d);
@@ -699,7 +731,16 @@ int64_t orc_fill(const orc_tables* te, const orc_tables* tn, int dist,
                  int dtype, uint64_t seed, uint64_t offset, uint64_t n,
                  const uint64_t* idx, void* out, uint8_t* words,
                  double* margin, int nthreads) {
+  return orc_fill_keyed(te, tn, dist, dtype, 0, seed, offset, n, idx, out, words, margin,
+                        nthreads);
+}
+
+int64_t orc_fill_keyed(const orc_tables* te, const orc_tables* tn, int dist,
+                       int dtype, int keying, uint64_t seed, uint64_t offset,
+                       uint64_t n, const uint64_t* idx, void* out,
+                       uint8_t* words, double* margin, int nthreads) {
   fill_job* jb = (fill_job*)calloc(1, sizeof(fill_job));
+  jb->keying = keying;
   jb->te = te;
   jb->tn = tn;
   jb->dist = dist;

@@ -100,7 +100,9 @@ int orc_build_tables(int dist, int ibits, int ubits, int abits,
  * (g_lo, g_hi, 0, a) and key (seed_lo, seed_hi).  A scripted source yields
  * a fixed list and flags an overrun when it runs out. */
 typedef struct orc_words {
-  int kind; /* 0 = philox, 1 = scripted */
+  int kind; /* 0 = philox, 1 = scripted, 2 = packed (K2) */
+  int dtype; /* packed source: the precision whose first word it forms */
+  uint32_t dom; /* philox: counter word 2 of every block */
   uint64_t seed, g;
   uint32_t block;
   int half;
@@ -111,6 +113,16 @@ typedef struct orc_words {
 } orc_words;
 
 void orc_words_philox(orc_words* w, uint64_t seed, uint64_t g);
+/* Packed keying (K2, opt-in; not the paper's, which allows any uniform
+ * source).  The first word of counter g comes from a block shared by
+ * neighbouring counters: FP64 -- half (g & 1) of block (h_lo, h_hi, 0, 0)
+ * with h = g >> 1 (half 0 = r0 | r1<<32, half 1 = r2 | r3<<32); FP32 --
+ * the 32-bit output r_(g & 3) of block (h_lo, h_hi, 0, 0) with h = g >> 2,
+ * L, presented as the word (L & 0x1FF) | (L >> 9) << 41 (layer index and
+ * sign from its low 9 bits, U from its top 23).  Every later word comes
+ * from counter g's private domain: blocks (g_lo, g_hi, 1, a), a = 0, 1, ...,
+ * words r0 | r1<<32 then r2 | r3<<32. */
+void orc_words_packed(orc_words* w, uint64_t seed, uint64_t g, int dtype);
 void orc_words_script(orc_words* w, const uint64_t* script, int n);
 uint64_t orc_next(orc_words* w);
 
@@ -152,6 +164,12 @@ int64_t orc_fill(const orc_tables* te, const orc_tables* tn, int dist,
                  int dtype, uint64_t seed, uint64_t offset, uint64_t n,
                  const uint64_t* idx, void* out, uint8_t* words,
                  double* margin, int nthreads);
+/* orc_fill with a choice of keying: 0 = per-index words (orc_words_philox),
+ * 1 = packed keying (orc_words_packed). */
+int64_t orc_fill_keyed(const orc_tables* te, const orc_tables* tn, int dist,
+                       int dtype, int keying, uint64_t seed, uint64_t offset,
+                       uint64_t n, const uint64_t* idx, void* out,
+                       uint8_t* words, double* margin, int nthreads);
 
 /* Fused reduction reference: sums[k] = sum x^(k+1), abssums[k] =
  * sum |x|^(k+1) for k = 0..3 accumulated in binary128, and a histogram of

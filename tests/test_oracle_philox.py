@@ -55,7 +55,7 @@ def _cases():
 
 def test_philox_matches_aten_engine(orc, aten):
     cases = _cases()
-    inp = "\n".join(f"{s} {g} {a}" for s, g, a in cases) + "\n"
+    inp = "\n".join(f"{s} {g} {a} 0" for s, g, a in cases) + "\n"
     out = subprocess.run([aten], input=inp, capture_output=True, text=True, check=True).stdout
     ref = [tuple(int(v) for v in line.split()) for line in out.strip().splitlines()]
     assert len(ref) == len(cases)
@@ -81,3 +81,41 @@ def test_philox_bits_uniform(orc):
     for b in range(64):
         ones = int(((w >> np.uint64(b)) & np.uint64(1)).sum())
         assert abs(ones - n / 2) < 5 * np.sqrt(n / 4), b
+
+
+def _aten_blocks(aten, rows):
+    """ATen's blocks for (seed, g, attempt, domain) rows."""
+    inp = "\n".join(f"{s} {g} {a} {d}" for s, g, a, d in rows) + "\n"
+    out = subprocess.run([aten], input=inp, capture_output=True, text=True, check=True).stdout
+    return [tuple(int(v) for v in line.split()) for line in out.strip().splitlines()]
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_packed_word_stream_matches_aten(orc, aten, dtype):
+    """Packed keying: the first word of counter g is taken from the block of
+    g >> 1 (FP64: half g & 1) or g >> 2 (FP32: 32-bit output g & 3, its low
+    9 bits kept and its top 23 bits moved to bits 41-63); later words are
+    counter g's private stream, blocks (g_lo, g_hi, 1, a).  Raw blocks come
+    from the independent ATen engine."""
+    rng = np.random.default_rng(20260 + dtype)
+    gs = [0, 1, 2, 3, 4, 5, 2**32 - 1, 2**32, 2**32 + 2, 2**64 - 1, 2**64 - 4]
+    gs += [int(v) for v in rng.integers(0, 2**63, size=200)]
+    seeds = [0x0123456789ABCDEF, 0, 2**64 - 1]
+    for seed in seeds:
+        shift = 1 if dtype == 1 else 2
+        rows = []
+        for g in gs:
+            rows.append((seed, g >> shift, 0, 0))
+            rows += [(seed, g, a, 1) for a in range(2)]
+        ref = _aten_blocks(aten, rows)
+        for k, g in enumerate(gs):
+            fast, p0, p1 = ref[3 * k], ref[3 * k + 1], ref[3 * k + 2]
+            words = orc.packed_words(seed, g, dtype, 5)
+            if dtype == 1:
+                h = g & 1
+                assert words[0] == fast[2 * h] | (fast[2 * h + 1] << 32), (seed, g)
+            else:
+                lane = fast[g & 3]
+                assert words[0] == (lane & 0x1FF) | ((lane >> 9) << 41), (seed, g)
+            assert words[1:] == [p0[0] | (p0[1] << 32), p0[2] | (p0[3] << 32),
+                                 p1[0] | (p1[1] << 32), p1[2] | (p1[3] << 32)], (seed, g)

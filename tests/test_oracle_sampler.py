@@ -284,9 +284,11 @@ def _equiprob_edges(dist, k=1024):
     return -np.log1p(-q) if dist == 0 else special.ndtri(q)
 
 
+@pytest.mark.parametrize("keying", [0, 1])
 @pytest.mark.parametrize("dist,dtype", [(0, 1), (1, 1), (0, 0), (1, 0)])
-def test_distribution_full_width(orc, dist, dtype):
-    x, errs, words, _ = orc.fill(dist, dtype, SEED, 0, N_STAT, want_words=True)
+def test_distribution_full_width(orc, dist, dtype, keying):
+    """Per-index keying (0) and packed keying (1) give the same laws."""
+    x, errs, words, _ = orc.fill(dist, dtype, SEED, 0, N_STAT, want_words=True, keying=keying)
     assert errs == 0 and np.all(np.isfinite(x))
     x = x.astype(np.float64)
     # KS against the closed-form CDF
