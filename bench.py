@@ -44,6 +44,9 @@ def parse_args():
     p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
     p.add_argument("--n", type=int, default=None,
                    help="override the per-step size (for small profiling captures)")
+    p.add_argument("--keying", default="index", choices=["index", "packed"],
+                   help="uniform keying: per-index (the default, zig_exponential/zig_normal) "
+                        "or the opt-in packed keying (zig_generate ZIG_KEY_PACKED)")
     p.add_argument("--no-tune", action="store_true",
                    help="skip the launch-shape autotuner (use the default shape)")
     p.add_argument("--batch-requests", type=int, default=None,
@@ -215,7 +218,11 @@ def run_zig(args):
     n = args.n or c["n"]
     tdt = torch.float64 if c["dtype"] == W.F64 else torch.float32
     esize = 8 if c["dtype"] == W.F64 else 4
-    fn = z.zig_normal if c["dist"] == W.NORMAL else z.zig_exponential
+    if args.keying == "packed":
+        def fn(out_, n_, seed_, offset_, stream=None):
+            z.zig_generate(c["dist"], z.ZIG_KEY_PACKED, out_, n_, seed_, offset_, stream=stream)
+    else:
+        fn = z.zig_normal if c["dist"] == W.NORMAL else z.zig_exponential
     out = torch.empty(n, dtype=tdt, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -223,7 +230,7 @@ def run_zig(args):
         return step_counter(c["offset"], step, rank, world, n)
 
     tuned = None
-    if not args.no_tune:
+    if not args.no_tune and args.keying == "index":
         # pick the launch shape on the workload's own output buffer (> L2)
         chosen, results = z.zig_autotune(c["dist"], c["dtype"], out, reps=3, stream=stream)
         tuned = {"chosen": chosen, "measured": results}
@@ -265,12 +272,19 @@ def run_zig(args):
         "clocks": clk.summary(),
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(n),
+                     "frac": achieved / peak,
+                     "traffic": recorded_traffic(n) if (args.keying == "index" and
+                                                        args.workload == DEFAULT_WORKLOAD) else None,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, copy)",
-                     "kernel": "gen_kernel<normal,double>",
+                     "kernel": "gen_kernel<{},{}{}>".format(
+                         "normal" if c["dist"] else "exp",
+                         "double" if c["dtype"] == W.F64 else "float",
+                         ",packed" if args.keying == "packed" else ""),
                      "algorithmic_bytes_per_launch": n * esize},
         "device_status": z.zig_strerror(status),
-        "launch_shape": z.zig_tune_get(c["dist"], c["dtype"]),
+        "launch_shape": z.zig_tune_get(c["dist"], c["dtype"]) if args.keying == "index"
+        else "default",
+        "keying": args.keying,
     }
     if tuned is not None:
         line["autotune"] = tuned
@@ -279,6 +293,7 @@ def run_zig(args):
     if rank == 0 and world == 1 and not args.no_extras:
         line["cpu_baseline"] = cpu_baseline(c)
         line["variants"] = measure_variants(z, stream)
+        line["packed_keying"] = measure_packed(z, stream)
         del out
         torch.cuda.empty_cache()
         line["batch"] = measure_batch(z, stream)
@@ -345,6 +360,39 @@ def measure_variants(z, stream, steps: int = 100):
         res[name] = {"gsamples_s": n / (ms / 1e3) / 1e9, "gb_s": n * es / (ms / 1e3) / 1e9,
                      "ms_per_launch": ms, "launch_shape": chosen}
         del buf
+    return res
+
+
+def measure_packed(z, stream, steps: int = 100):
+    """Packed keying (opt-in, different outputs): the four dist/dtype pairs
+    at 2^28 counters each through zig_generate, with the HBM-write roofline
+    fraction of each against the measured copy peak."""
+    import torch
+
+    peak, _ = measured_peak()
+    res = {}
+    n = 1 << 28
+    for name, dist, dtype in (("exp_f64", W.EXP, W.F64), ("normal_f64", W.NORMAL, W.F64),
+                              ("exp_f32", W.EXP, W.F32), ("normal_f32", W.NORMAL, W.F32)):
+        tdt = torch.float64 if dtype == W.F64 else torch.float32
+        es = 8 if dtype == W.F64 else 4
+        buf = torch.empty(n, dtype=tdt, device="cuda")
+        for k in range(5):
+            z.zig_generate(dist, z.ZIG_KEY_PACKED, buf, n, W.SEED, k * n, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            z.zig_generate(dist, z.ZIG_KEY_PACKED, buf, n, W.SEED, (k + 5) * n, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        gbs = n * es / (ms / 1e3) / 1e9
+        res[name] = {"gsamples_s": n / (ms / 1e3) / 1e9, "gb_s": gbs, "ms_per_launch": ms,
+                     "roofline_frac": gbs / peak}
+        del buf
+    res["note"] = ("ZIG_KEY_PACKED: one Philox block per 2 FP64 / 4 FP32 fast words; "
+                   "outputs differ from per-index keying and are checked against the "
+                   "oracle's packed word source")
     return res
 
 

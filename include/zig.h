@@ -272,6 +272,37 @@ zig_status zig_status_poll(void* stream);
 zig_status zig_set_fringe_limits(int max_attempts, int max_tail);
 
 /*
+ * Keying of the uniform words.  ZIG_KEY_INDEX is the scheme above (every
+ * output's words from its own counter: one Philox block per output on the
+ * fast path); zig_exponential and zig_normal use it.  ZIG_KEY_PACKED (opt-in,
+ * different outputs) shares one block between the fast words of 2 FP64 or
+ * 4 FP32 neighbouring outputs, keeping every variate a function of (seed, g)
+ * alone:
+ *   - the first word of counter g: FP64, half (g & 1) of Philox((h_lo, h_hi,
+ *     0, 0)) with h = g >> 1 (half 0 = r0 | r1 << 32, half 1 = r2 | r3 << 32);
+ *     FP32, the 32-bit output r_(g & 3) of Philox((h_lo, h_hi, 0, 0)) with
+ *     h = g >> 2, whose bits 0-7 are i, bit 8 the normal's sign and bits 9-31
+ *     U (m 2^-23);
+ *   - every later word (alias pick, overhang attempts, tails): counter g's
+ *     private stream, blocks Philox((g_lo, g_hi, 1, a)), a = 0, 1, ..., words
+ *     r0 | r1 << 32 then r2 | r3 << 32.
+ * The method (Table 1) is unchanged; the paper lets any uniform source feed
+ * it (Sec. 2).  Split invariance holds as for ZIG_KEY_INDEX.
+ */
+typedef enum { ZIG_KEY_INDEX = 0, ZIG_KEY_PACKED = 1 } zig_keying;
+
+/*
+ * zig_generate -- zig_exponential (dist ZIG_EXP) or zig_normal (ZIG_NORMAL)
+ * with a choice of keying; ZIG_KEY_INDEX gives exactly their outputs.
+ * Arguments, layout and returns as theirs, plus ZIG_E_INVAL for an unknown
+ * dist or keying.  With ZIG_KEY_PACKED a launch whose first vector-aligned
+ * counter (offset + the unaligned head) is not a multiple of 2 (FP64) or 4
+ * (FP32) still gives the same outputs, computing one block per output.
+ */
+zig_status zig_generate(zig_dist dist, zig_keying keying, void* out, uint64_t n, uint64_t seed,
+                        uint64_t offset, zig_dtype dtype, void* stream);
+
+/*
  * Launch-shape autotuning.  The paper tunes its CPU code by hand and has
  * no counterpart; the shapes below change only how the work is spread over
  * the GPU, never the outputs (element t is always the variate of counter

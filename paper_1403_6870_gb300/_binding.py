@@ -64,6 +64,8 @@ _export_tables = _sig("zig_export_tables", _int, [_int, ctypes.POINTER(zig_table
 _exponential = _sig("zig_exponential", _int, [_vp, _u64, _u64, _u64, _int, _vp])
 _normal = _sig("zig_normal", _int, [_vp, _u64, _u64, _u64, _int, _vp])
 _status_poll = _sig("zig_status_poll", _int, [_vp])
+_generate = _sig("zig_generate", _int, [_int, _int, _vp, _u64, _u64, _u64, _int, _vp])
+ZIG_KEY_INDEX, ZIG_KEY_PACKED = 0, 1
 _moments_ws = _sig("zig_moments_workspace_bytes", ctypes.c_size_t, [_int, _int])
 _moments = _sig("zig_moments", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp, _vp,
                                       ctypes.c_size_t, _vp])
@@ -155,6 +157,15 @@ def zig_normal(out, n=None, seed: int = 0, offset: int = 0, dtype=None, stream=N
     ptr, n, code = _out_args(out, n, dtype)
     _check(_normal(ptr, n, seed & (2**64 - 1), offset & (2**64 - 1), code,
                    _stream_handle(stream, out)), "zig_normal")
+
+
+def zig_generate(dist: int, keying: int, out, n=None, seed: int = 0, offset: int = 0, dtype=None,
+                 stream=None) -> None:
+    """zig_exponential / zig_normal with a keying (ZIG_KEY_INDEX or
+    ZIG_KEY_PACKED)."""
+    ptr, n, code = _out_args(out, n, dtype)
+    _check(_generate(int(dist), int(keying), ptr, n, seed & (2**64 - 1), offset & (2**64 - 1),
+                     code, _stream_handle(stream, out)), "zig_generate")
 
 
 def zig_moments_workspace_bytes(dist: int, dtype: int) -> int:
@@ -298,5 +309,6 @@ def raw_call(name: str, *args) -> int:  # noqa: C901
     """Call an exported function with raw C arguments and return its status
     (used to exercise argument checks without raising)."""
     table = {"zig_exponential": _exponential, "zig_normal": _normal, "zig_moments": _moments,
+             "zig_generate": _generate,
              "zig_set_fringe_limits": _set_limits, "zig_status_poll": _status_poll}
     return int(table[name](*args))

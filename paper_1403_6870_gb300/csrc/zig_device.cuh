@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "zig.h"
 
@@ -105,9 +106,29 @@ __device__ __forceinline__ uint2 philox_rounds3to10_first(uint32_t c0, uint32_t 
   return make_uint2(c0, c1);
 }
 
-// Full block k of counter g (domain 0) with the round keys.
-__device__ __forceinline__ uint4 philox_block(uint64_t g, uint32_t k, const RoundKeys& rk) {
-  uint32_t c0 = (uint32_t)g, c1 = (uint32_t)(g >> 32), c2 = 0u, c3 = k;
+// Rounds 3..10 given the state after round 2, returning the whole block.
+__device__ __forceinline__ uint4 philox_rounds3to10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                    uint32_t c3, const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)kM0 * c0;
+    const uint64_t p1 = (uint64_t)kM1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Full block k of counter g in domain dom (counter word 2) with the round
+// keys: dom 0 is the per-index stream, dom 1 the private stream of packed
+// keying.
+__device__ __forceinline__ uint4 philox_block(uint64_t g, uint32_t k, const RoundKeys& rk,
+                                              uint32_t dom = 0u) {
+  uint32_t c0 = (uint32_t)g, c1 = (uint32_t)(g >> 32), c2 = dom, c3 = k;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint64_t p0 = (uint64_t)kM0 * c0;
@@ -162,6 +183,45 @@ struct Words {
     half = false;
     ++blk;
     return pack(r2, r3);
+  }
+};
+
+// Packed keying (opt-in; ZIG_KEY_PACKED in zig.h): the first word of
+// counter g comes from a block shared with its neighbours, FP64: half
+// (g & 1) of block (g >> 1, dom 0, attempt 0); FP32: 32-bit output (g & 3)
+// of block (g >> 2, ...), L, as the word (L & 0x1FF) | (L >> 9) << 41 (the
+// layer index and sign from L's low 9 bits, U from its top 23).  Every later
+// word comes from counter g's private stream Words(seed, g, 1).
+template <typename T>
+__device__ __forceinline__ uint64_t packed_word_of(uint4 b, uint64_t g) {
+  if (sizeof(T) == 8) return (g & 1u) ? pack(b.z, b.w) : pack(b.x, b.y);
+  const uint32_t q = (uint32_t)g & 3u;
+  const uint32_t lane = q == 0 ? b.x : q == 1 ? b.y : q == 2 ? b.z : b.w;
+  return (uint64_t)(lane & 0x1FFu) | ((uint64_t)(lane >> 9) << 41);
+}
+
+template <typename T>
+__device__ __forceinline__ uint64_t packed_first(uint64_t g, const RoundKeys& rk) {
+  return packed_word_of<T>(philox_block(g >> (sizeof(T) == 8 ? 1 : 2), 0u, rk), g);
+}
+
+template <typename T>
+struct PackedWords {
+  Words rest;
+  uint64_t first;
+  bool started;
+  __device__ PackedWords(uint64_t seed, uint64_t g) : rest(seed, g, 1u), started(false) {
+    const uint64_t h = g >> (sizeof(T) == 8 ? 1 : 2);
+    first = packed_word_of<T>(
+        philox10((uint32_t)h, (uint32_t)(h >> 32), 0u, 0u, (uint32_t)seed, (uint32_t)(seed >> 32)),
+        g);
+  }
+  __device__ uint64_t next() {
+    if (!started) {
+      started = true;
+      return first;
+    }
+    return rest.next();
   }
 };
 
@@ -295,8 +355,8 @@ __device__ __forceinline__ bool overhang_attempt(const DevTab& t, int j,
 // innermost first, so depth d adds X_0 d times after the final draw.
 // Steps 5-8 keep j on rejection and draw fresh (ux, uy); the first attempt
 // reuses U_1 as ux (its bits are disjoint from i).
-template <typename T>
-__device__ T exp_general(Words& w, const DevTab& t, Limits lim, bool& err) {
+template <typename T, typename W>
+__device__ T exp_general(W& w, const DevTab& t, Limits lim, bool& err) {
   typedef Prec<T> P;
   int depth = 0;
   T x;
@@ -336,8 +396,8 @@ __device__ T exp_general(Words& w, const DevTab& t, Limits lim, bool& err) {
 // beyond X_0 by Marsaglia-Tsang from two exponential draws (a = E_1 / X_0,
 // accept when 2 E_2 > a^2, return X_0 + a); overhangs by rejection against
 // e^{-x^2/2}, keeping j and redrawing both uniforms.
-template <typename T>
-__device__ T normal_general(Words& w, const DevTab& te, const DevTab& tn, Limits lim,
+template <typename T, typename W>
+__device__ T normal_general(W& w, const DevTab& te, const DevTab& tn, Limits lim,
                             bool& err) {
   typedef Prec<T> P;
   const uint64_t w0 = w.next();
@@ -379,10 +439,11 @@ __device__ T normal_general(Words& w, const DevTab& te, const DevTab& tn, Limits
   return negative ? -x : x;
 }
 
-// The complete sampler for counter g of key seed.
-template <int DIST, typename T>
+// The complete sampler for counter g of key seed; KEY 0: per-index words,
+// KEY 1: packed keying.
+template <int DIST, typename T, int KEY = 0>
 __device__ __noinline__ T sample_general(uint64_t seed, uint64_t g, Limits lim) {
-  Words w(seed, g);
+  typename std::conditional<KEY == 0, Words, PackedWords<T>>::type w(seed, g);
   bool err = false;
   T x = (DIST == ZIG_EXP)
             ? exp_general<T>(w, g_tab[ZIG_EXP], lim, err)

@@ -117,6 +117,19 @@ struct GenShape<double> : Shape<ZIG_GEN_V64, ZIG_GEN_R64, ZIG_GEN_MINBLOCKS> {};
 template <>
 struct GenShape<float> : Shape<ZIG_GEN_V32, ZIG_GEN_R32, ZIG_GEN_MINBLOCKS> {};
 
+// Default shapes of packed keying: a Philox block makes 2 FP64 / 4 FP32
+// outputs, so a thread makes more outputs per tile (FP32: 32) to spread the
+// tile's fixed costs; measured on GB300 against R = 1, 2 and V = 4.
+#ifndef ZIG_PACKED_R32
+#define ZIG_PACKED_R32 4
+#endif
+template <typename T>
+struct PackedShape;
+template <>
+struct PackedShape<double> : Shape<ZIG_GEN_V64, ZIG_GEN_R64, ZIG_GEN_MINBLOCKS> {};
+template <>
+struct PackedShape<float> : Shape<ZIG_GEN_V32, ZIG_PACKED_R32, ZIG_GEN_MINBLOCKS> {};
+
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -147,6 +160,13 @@ struct RunState {
     const uint64_t u = (uint64_t)kM0 * ((uint32_t)(g0 >> 32) ^ rk.k0[0]);
     uhi = (uint32_t)(u >> 32) ^ rk.k1[1];
     ulo = (uint32_t)u;
+  }
+  // block 0 (attempt 0) of counter g0 + d (no wrap of the low word)
+  __device__ __forceinline__ uint4 block(uint32_t d, const RoundKeys& rk) const {
+    const uint64_t p = base + (uint64_t)kM0 * d;
+    const uint32_t n2 = (uint32_t)(p >> 32) ^ rk.k1[0], n3 = (uint32_t)p;
+    const uint64_t p1 = (uint64_t)kM1 * n2;  // round 2
+    return philox_rounds3to10((uint32_t)(p1 >> 32) ^ rk.k0[1], (uint32_t)p1, uhi ^ n3, ulo, rk);
   }
   // first word of block 0 for counter g0 + d (no wrap of the low word)
   __device__ __forceinline__ uint2 word(uint32_t d, const RoundKeys& rk) const {
@@ -340,7 +360,10 @@ __device__ __forceinline__ int claim(bool f, int& n) {
 // Block 0 gives U_1 (as ux) and the alias word; block 1's first word gives
 // uy.  Tail draws (j = 0) and whole-sampler items go to the tail queue;
 // rejected attempts to the retry queue with their state.
-template <int DIST, typename T, uint64_t kPosMask, typename Sink, typename State>
+// KEY 0 (per-index words): block 0 gives U_1 (as ux) and the alias word,
+// block 1's first word uy.  KEY 1 (packed keying): U_1 from the packed
+// first word, the alias word and uy from private block 0.
+template <int DIST, typename T, uint64_t kPosMask, int KEY, typename Sink, typename State>
 __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const RoundKeys& rk,
                                           Limits lim, bool active, uint64_t item, State& sh,
                                           SideCounts& c) {
@@ -349,25 +372,38 @@ __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const Rou
   const bool whole = (item & kWholeTag) != 0;
   const uint64_t p = item & ~kWholeTag;  // the queued value
   const uint64_t g = offset + (p & kPosMask);
-  const uint4 b0 = philox_block(g, 0u, rk);
-  const uint64_t w0 = pack(b0.x, b0.y);
-  const int j = alias_pick(t, pack(b0.z, b0.w));
+  uint64_t w0, aw;
+  uint4 b1 = make_uint4(0u, 0u, 0u, 0u);
+  if (KEY == 0) {
+    const uint4 b0 = philox_block(g, 0u, rk);
+    w0 = pack(b0.x, b0.y);
+    aw = pack(b0.z, b0.w);
+  } else {
+    w0 = packed_first<T>(g, rk);
+    b1 = philox_block(g, 0u, rk, 1u);
+    aw = pack(b1.x, b1.y);
+  }
+  const int j = alias_pick(t, aw);
   const bool negative = ((w0 >> 8) & 1u) != 0;
   const bool overhang = active && !whole && j != 0;
   bool retry = false;
   uint64_t state = 0, next = 0;
   if (overhang) {
-    const uint4 b1 = philox_block(g, 1u, rk);
+    if (KEY == 0) b1 = philox_block(g, 1u, rk);
+    const uint64_t wy = KEY == 0 ? pack(b1.x, b1.y) : pack(b1.z, b1.w);
     T x;
-    if (overhang_attempt<DIST, T>(t, j, P::ubits(w0), P::ubits(pack(b1.x, b1.y)), x)) {
+    if (overhang_attempt<DIST, T>(t, j, P::ubits(w0), P::ubits(wy), x)) {
       put_signed<DIST, T>(sink, p, x, negative);
     } else if (1 >= lim.max_att) {
       sink.put(p, P::nan());
       atomicOr(&g_status, kLoopLimitBit);
     } else {
       retry = true;
-      state = (uint64_t)j | ((uint64_t)negative << 8) | (1ull << 9) | (2ull << 32);
-      next = pack(b1.z, b1.w);
+      // next block: per-index 2 (block 1's second word saved as the next
+      // ux); packed: private block 1
+      state = (uint64_t)j | ((uint64_t)negative << 8) | (1ull << 9) |
+              ((KEY == 0 ? 2ull : 1ull) << 32);
+      next = KEY == 0 ? pack(b1.z, b1.w) : 0ull;
     }
   }
   const bool tl = active && !overhang;
@@ -386,7 +422,7 @@ __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const Rou
 // is kept (Table 1 step 8 returns to step 4).  State: j in bits 0-7, the
 // normal's sign in bit 8, completed attempts in bits 9-31, next block in
 // bits 32-63.
-template <int DIST, typename T, uint64_t kPosMask, typename Sink, typename State>
+template <int DIST, typename T, uint64_t kPosMask, int KEY, typename Sink, typename State>
 __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const RoundKeys& rk,
                                             Limits lim, bool active, uint64_t p,
                                             uint64_t state, uint64_t word, State& sh,
@@ -400,9 +436,13 @@ __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const R
   bool retry = false;
   uint64_t nstate = 0, next = 0;
   if (active) {
-    const uint4 b = philox_block(offset + (p & kPosMask), blk, rk);
+    // per-index: ux is the saved word, uy block blk's first word; packed:
+    // both from private block blk
+    const uint4 b = philox_block(offset + (p & kPosMask), blk, rk, KEY == 0 ? 0u : 1u);
+    const uint64_t wx = KEY == 0 ? word : pack(b.x, b.y);
+    const uint64_t wy = KEY == 0 ? pack(b.x, b.y) : pack(b.z, b.w);
     T x;
-    if (overhang_attempt<DIST, T>(t, j, P::ubits(word), P::ubits(pack(b.x, b.y)), x)) {
+    if (overhang_attempt<DIST, T>(t, j, P::ubits(wx), P::ubits(wy), x)) {
       put_signed<DIST, T>(sink, p, x, negative);
     } else if ((int)(att + 1) >= lim.max_att) {
       sink.put(p, P::nan());
@@ -410,7 +450,7 @@ __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const R
     } else {
       retry = true;
       nstate = (state & 0x1FFull) | ((uint64_t)(att + 1) << 9) | ((uint64_t)(blk + 1) << 32);
-      next = pack(b.z, b.w);
+      next = KEY == 0 ? pack(b.z, b.w) : 0ull;
     }
   }
   const int k = claim(retry, c.retry);
@@ -424,7 +464,7 @@ __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const R
 // Consumer: run the retry and tail stages while they hold `need` or more
 // entries (at most 32 per batch).  Each side queue holds fewer than 32
 // entries before a stage-1 batch, so it stays within its 64 slots.
-template <int DIST, typename T, typename Sink, typename State>
+template <int DIST, typename T, int KEY, typename Sink, typename State>
 __device__ __forceinline__ void side_stages(Sink& sink, uint64_t seed, uint64_t offset,
                                             const RoundKeys& rk, Limits lim, int need,
                                             State& sh, SideCounts& c) {
@@ -439,14 +479,14 @@ __device__ __forceinline__ void side_stages(Sink& sink, uint64_t seed, uint64_t 
                      w = active ? sh.rw[k] : 0;
       c.retry -= take;
       __syncwarp();  // slots read before they are refilled
-      stage_retry<DIST, T, kPos>(sink, offset, rk, lim, active, p, st, w, sh, c);
+      stage_retry<DIST, T, kPos, KEY>(sink, offset, rk, lim, active, p, st, w, sh, c);
     } else if (c.tail >= need) {
       const int take = c.tail < 32 ? c.tail : 32;
       const bool active = lane < take;
       const uint64_t p = active ? sh.tq[c.tail - take + lane] : 0;
       c.tail -= take;
       __syncwarp();
-      if (active) sink.put(p, sample_general<DIST, T>(seed, offset + p, lim));
+      if (active) sink.put(p, sample_general<DIST, T, KEY>(seed, offset + p, lim));
     } else {
       break;
     }
@@ -458,6 +498,10 @@ __device__ __forceinline__ void side_stages(Sink& sink, uint64_t seed, uint64_t 
 #define ZIG_GEN_UNROLL_R 1
 #endif
 constexpr int kUnrollR = ZIG_GEN_UNROLL_R;
+#ifndef ZIG_PACKED_UNROLL_R
+#define ZIG_PACKED_UNROLL_R 4
+#endif
+constexpr int kPackedUnrollR = ZIG_PACKED_UNROLL_R;
 
 // Steps 1-2 for one producer thread's S = V R outputs of a tile: vector r
 // holds counters g0 + r kPThreads V + [0, V) and is vector v0 + r kPThreads
@@ -483,6 +527,64 @@ __device__ __forceinline__ unsigned producer_tile(Sink& sink, uint64_t g0, uint6
       const uint2 w = NOWRAP ? run.word(d, rk) : philox_first(g0 + d, rk);
       v[k] = fast_value<DIST>(w.x, w.y, sX);
       f |= (unsigned)((w.x & 0xFFu) >= L) << k;
+    }
+    const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
+    if (full || vi < nvec) {
+      sink.template vec<V>(vi, v, f);
+      fm |= f << (r * V);
+    }
+  }
+  sink.tile_end();
+  return fm;
+}
+
+// Packed keying (KEY 1) for one producer thread's tile: each Philox block
+// gives B = V / P whole outputs (P = 2 FP64 words or 4 FP32 lanes), so a
+// vector takes V / P blocks.  MODE 0: the vector's counters start at a
+// multiple of P and the run's block counters do not wrap their low word;
+// MODE 1: aligned, with wrap; MODE 2: not aligned (one block per output).
+template <int DIST, typename T, typename Shp, int MODE, typename Sink>
+__device__ __forceinline__ unsigned producer_tile_packed(Sink& sink, uint64_t g0, uint64_t v0,
+                                                         uint64_t nvec, bool full,
+                                                         const RoundKeys& rk, const T* sX,
+                                                         uint32_t L) {
+  constexpr int V = Shp::V, R = Shp::R;
+  constexpr int P = sizeof(T) == 8 ? 2 : 4, SH = sizeof(T) == 8 ? 1 : 2, B = V / P;
+  static_assert(V % P == 0, "a vector holds whole blocks");
+  unsigned fm = 0;
+  const uint64_t h0 = g0 >> SH;
+  const RunState run(h0, rk);
+#pragma unroll kPackedUnrollR
+  for (int r = 0; r < R; ++r) {
+    T v[V];
+    unsigned f = 0;
+    if (MODE != 2) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const uint32_t d = (uint32_t)(r * kPThreads * B + b);
+        const uint4 w = MODE == 0 ? run.block(d, rk) : philox_block(h0 + d, 0u, rk);
+        if (sizeof(T) == 8) {
+          v[2 * b] = fast_value<DIST>(w.x, w.y, sX);
+          v[2 * b + 1] = fast_value<DIST>(w.z, w.w, sX);
+          f |= ((unsigned)((w.x & 0xFFu) >= L) | ((unsigned)((w.z & 0xFFu) >= L) << 1)) << (2 * b);
+        } else {
+          v[4 * b] = fast_value<DIST>(w.x, w.x, sX);
+          v[4 * b + 1] = fast_value<DIST>(w.y, w.y, sX);
+          v[4 * b + 2] = fast_value<DIST>(w.z, w.z, sX);
+          v[4 * b + 3] = fast_value<DIST>(w.w, w.w, sX);
+          f |= ((unsigned)((w.x & 0xFFu) >= L) | ((unsigned)((w.y & 0xFFu) >= L) << 1) |
+                ((unsigned)((w.z & 0xFFu) >= L) << 2) | ((unsigned)((w.w & 0xFFu) >= L) << 3))
+               << (4 * b);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const uint64_t g = g0 + (uint64_t)(r * kPThreads * V + k);
+        const uint64_t w = packed_word_of<T>(philox_block(g >> SH, 0u, rk), g);
+        v[k] = fast_value<DIST>((uint32_t)w, (uint32_t)(w >> 32), sX);
+        f |= (unsigned)(((uint32_t)w & 0xFFu) >= L) << k;
+      }
     }
     const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
     if (full || vi < nvec) {
@@ -522,7 +624,7 @@ struct ReduceOut {
 // returns once every published item has its final value, with sh.done
 // reset to zero and its ring cursor hd advanced past the items.  Returns
 // false if a bounded wait gave up.
-template <int DIST, typename T, typename Shp, typename Sink, typename State>
+template <int DIST, typename T, typename Shp, int KEY, typename Sink, typename State>
 __device__ __forceinline__ bool gen_tiles(State& sh, Sink& sink, const T* sX, uint64_t n,
                                           uint64_t head, uint64_t nvec, uint64_t seed,
                                           uint64_t offset, const RoundKeys& rk, Limits lim,
@@ -553,10 +655,21 @@ __device__ __forceinline__ bool gen_tiles(State& sh, Sink& sink, const T* sX, ui
       const uint64_t g0 = offset + p0;
       const bool full = (tile + 1) * kTile <= nvec;
       unsigned fm;  // outputs of this thread whose layer index is >= L_max
-      if ((uint32_t)g0 <= 0xFFFFFFFFu - kSpan)
-        fm = producer_tile<DIST, T, Shp, true>(sink, g0, v0, nvec, full, rk, sX, L);
-      else
-        fm = producer_tile<DIST, T, Shp, false>(sink, g0, v0, nvec, full, rk, sX, L);
+      if (KEY == 0) {
+        if ((uint32_t)g0 <= 0xFFFFFFFFu - kSpan)
+          fm = producer_tile<DIST, T, Shp, true>(sink, g0, v0, nvec, full, rk, sX, L);
+        else
+          fm = producer_tile<DIST, T, Shp, false>(sink, g0, v0, nvec, full, rk, sX, L);
+      } else {
+        constexpr int P = sizeof(T) == 8 ? 2 : 4, SH = sizeof(T) == 8 ? 1 : 2;
+        constexpr uint32_t kSpanB = (uint32_t)((R - 1) * kPThreads * (V / P) + (V / P - 1));
+        if (g0 % P != 0)
+          fm = producer_tile_packed<DIST, T, Shp, 2>(sink, g0, v0, nvec, full, rk, sX, L);
+        else if ((uint32_t)(g0 >> SH) <= 0xFFFFFFFFu - kSpanB)
+          fm = producer_tile_packed<DIST, T, Shp, 0>(sink, g0, v0, nvec, full, rk, sX, L);
+        else
+          fm = producer_tile_packed<DIST, T, Shp, 1>(sink, g0, v0, nvec, full, rk, sX, L);
+      }
       if (__any_sync(0xFFFFFFFFu, fm != 0)) {
         const unsigned fmask = fm;
         ok = publish(sh, __popc(fmask), [&](int k) {
@@ -609,9 +722,10 @@ __device__ __forceinline__ bool gen_tiles(State& sh, Sink& sink, const T* sX, ui
       __threadfence_block();
       __syncwarp();
       if (lane == 0) *(volatile unsigned*)&sh.head = hd;
-      stage_new<DIST, T, ~kWholeTag>(sink, offset, rk, lim, active, active ? item : 0, sh, c);
+      stage_new<DIST, T, ~kWholeTag, KEY>(sink, offset, rk, lim, active, active ? item : 0, sh,
+                                          c);
       __syncwarp();
-      side_stages<DIST, T>(sink, seed, offset, rk, lim, last ? 1 : 32, sh, c);
+      side_stages<DIST, T, KEY>(sink, seed, offset, rk, lim, last ? 1 : 32, sh, c);
       if (last) break;
       t0 = globaltimer();
     }
@@ -624,7 +738,7 @@ __device__ __forceinline__ bool gen_tiles(State& sh, Sink& sink, const T* sX, ui
 
 // One launch covers outputs [0, n) (layout as in gen_tiles); CTA b takes
 // tiles b, b + gridDim.x, ... and CTA 0 the head and tail elements.
-template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>>
+template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>, int KEY = 0>
 __global__ void __launch_bounds__(kThreads, Shp::MB)
     gen_kernel(Sink sink, uint64_t n, uint32_t head, uint64_t nvec, uint64_t seed,
                uint64_t offset, const RoundKeys rk, Limits lim, ReduceOut red) {
@@ -648,8 +762,8 @@ __global__ void __launch_bounds__(kThreads, Shp::MB)
 
   const uint64_t ntiles = (nvec + kTile - 1) / kTile;
   unsigned hd = 0;
-  gen_tiles<DIST, T, Shp>(sh, sink, sh.sX, n, head, nvec, seed, offset, rk, lim, blockIdx.x,
-                          ntiles, gridDim.x, blockIdx.x == 0, hd);
+  gen_tiles<DIST, T, Shp, KEY>(sh, sink, sh.sX, n, head, nvec, seed, offset, rk, lim,
+                               blockIdx.x, ntiles, gridDim.x, blockIdx.x == 0, hd);
 
   if constexpr (Sink::kReduce) {
     // CTA partials in thread order, then the CTA's histogram into the
@@ -778,13 +892,13 @@ RoundKeys round_keys(uint64_t seed) {
   return rk;
 }
 
-template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>>
+template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>, int KEY = 0>
 int occupancy_blocks(int dev) {
   static std::atomic<int> cache[kMaxDevices];
   int v = cache[dev].load(std::memory_order_relaxed);
   if (v > 0) return v;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gen_kernel<DIST, T, Sink, Shp>,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gen_kernel<DIST, T, Sink, Shp, KEY>,
                                                     kThreads, 0) != cudaSuccess ||
       occ < 1) {
     cudaGetLastError();
@@ -796,7 +910,7 @@ int occupancy_blocks(int dev) {
 
 // Materialising launch of shape Shp with at most bps CTAs per SM (0: as
 // many as fit).
-template <int DIST, typename T, typename Shp>
+template <int DIST, typename T, typename Shp, int KEY = 0>
 zig_status launch_gen(void* out, uint64_t n, uint64_t seed, uint64_t offset,
                       cudaStream_t stream, int dev, int bps) {
   constexpr int V = Shp::V, R = Shp::R;
@@ -805,14 +919,14 @@ zig_status launch_gen(void* out, uint64_t n, uint64_t seed, uint64_t offset,
   const uint64_t head = align_elems < n ? align_elems : n;
   const uint64_t nvec = (n - head) / V;
   const uint64_t tiles = (nvec + (uint64_t)kPThreads * R - 1) / ((uint64_t)kPThreads * R);
-  int occ = occupancy_blocks<DIST, T, StoreSink<T>, Shp>(dev);
+  int occ = occupancy_blocks<DIST, T, StoreSink<T>, Shp, KEY>(dev);
   if (bps > 0 && bps < occ) occ = bps;
   const uint64_t cap = (uint64_t)g_dev[dev].sms * (uint64_t)occ;
   uint64_t grid = tiles < cap ? tiles : cap;
   if (grid < 1) grid = 1;
   Limits lim{g_max_att.load(), g_max_tail.load()};
   StoreSink<T> sink{(T*)out, head};
-  gen_kernel<DIST, T, StoreSink<T>, Shp><<<(unsigned)grid, kThreads, 0, stream>>>(
+  gen_kernel<DIST, T, StoreSink<T>, Shp, KEY><<<(unsigned)grid, kThreads, 0, stream>>>(
       sink, n, (uint32_t)head, nvec, seed, offset, round_keys(seed), lim, ReduceOut{});
   if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
   return ZIG_OK;
@@ -965,8 +1079,10 @@ void apply_cached(int dev) {
 }
 
 zig_status generate(int dist, void* out, uint64_t n, uint64_t seed, uint64_t offset,
-                    zig_dtype dtype, void* stream) {
+                    zig_dtype dtype, void* stream, int keying = ZIG_KEY_INDEX) {
   if (dtype != ZIG_F32 && dtype != ZIG_F64) return ZIG_E_INVAL;
+  if (dist != ZIG_EXP && dist != ZIG_NORMAL) return ZIG_E_INVAL;
+  if (keying != ZIG_KEY_INDEX && keying != ZIG_KEY_PACKED) return ZIG_E_INVAL;
   if (n == 0) return ZIG_OK;
   if (out == nullptr) return ZIG_E_INVAL;
   const size_t es = dtype == ZIG_F64 ? 8 : 4;
@@ -978,6 +1094,17 @@ zig_status generate(int dist, void* out, uint64_t n, uint64_t seed, uint64_t off
   if (st != ZIG_OK) return st;
   if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
   cudaStream_t s = (cudaStream_t)stream;
+  if (keying == ZIG_KEY_PACKED) {
+    if (dist == ZIG_EXP)
+      return dtype == ZIG_F64 ? launch_gen<ZIG_EXP, double, PackedShape<double>, 1>(
+                                    out, n, seed, offset, s, dev, 0)
+                              : launch_gen<ZIG_EXP, float, PackedShape<float>, 1>(
+                                    out, n, seed, offset, s, dev, 0);
+    return dtype == ZIG_F64 ? launch_gen<ZIG_NORMAL, double, PackedShape<double>, 1>(
+                                  out, n, seed, offset, s, dev, 0)
+                            : launch_gen<ZIG_NORMAL, float, PackedShape<float>, 1>(
+                                  out, n, seed, offset, s, dev, 0);
+  }
   const Selection& sel = g_dev[dev].sel[dist == ZIG_EXP ? 0 : 1][dtype == ZIG_F64 ? 1 : 0];
   const int k = sel.variant.load(std::memory_order_relaxed);
   const int bps = sel.bps.load(std::memory_order_relaxed);
@@ -1196,6 +1323,11 @@ zig_status zig_exponential(void* out, uint64_t n, uint64_t seed, uint64_t offset
 zig_status zig_normal(void* out, uint64_t n, uint64_t seed, uint64_t offset, zig_dtype dtype,
                       void* stream) {
   return generate(ZIG_NORMAL, out, n, seed, offset, dtype, stream);
+}
+
+zig_status zig_generate(zig_dist dist, zig_keying keying, void* out, uint64_t n, uint64_t seed,
+                        uint64_t offset, zig_dtype dtype, void* stream) {
+  return generate(dist, out, n, seed, offset, dtype, stream, keying);
 }
 
 size_t zig_moments_workspace_bytes(zig_dist dist, zig_dtype dtype) {
