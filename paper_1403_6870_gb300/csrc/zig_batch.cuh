@@ -11,19 +11,18 @@
 // CTAs work on neighbouring tiles (mostly the same request, hence the same
 // instruction stream); a CTA whose range is exhausted claims chunks from the
 // other ranges in turn.  The tiles of one request inside a chunk form a
-// session: all eight warps run the plain kernel's producer/consumer code for
-// the request's (dist, dtype) with its key, offset and transform in
-// registers, and meet at a barrier once the session's fringe items are
-// final.  A counter per request (its tiles not yet finished) reaches zero
-// when the request is complete; the CTA that completes it records
-// %globaltimer minus the batch start.
+// session: all eight warps run the plain kernel's code for the request's
+// (dist, dtype) with its key, offset and transform in registers, and meet at
+// a barrier once each has finished its fringe draws.  A counter per request
+// (its tiles not yet finished) reaches zero when the request is complete;
+// the CTA that completes it records %globaltimer minus the batch start.
 #ifndef ZIG_BATCH_CUH
 #define ZIG_BATCH_CUH
 
 namespace zig {
 
-constexpr int kBatchReqBits = 23;  // request index in a ring item
-constexpr int kBatchPosBits = 40;  // element index in a ring item
+constexpr int kBatchReqBits = 23;  // requests per batch: below 2^23
+constexpr int kBatchPosBits = 40;  // variates per request: below 2^40
 constexpr uint64_t kBatchPosMask = (1ull << kBatchPosBits) - 1ull;
 constexpr unsigned kBatchInvalidBit = 1u << 10;  // status bit: a request was rejected
 
@@ -77,14 +76,11 @@ __host__ __device__ constexpr size_t batch_workspace_total(uint32_t count) {
 }
 
 // Shared state of one batch CTA: X_i of both distributions in both
-// precisions, the fringe ring and the consumer's side queues (the members
-// gen_tiles uses), and a flag set when a bounded wait gave up.
+// precisions and the warps' fringe queues (the members gen_tiles uses).
 struct BatchCtaState {
   double sX64[2][256];
   float sX32[2][256];
-  uint64_t ring[kRing];
-  unsigned tail, head, done, abort;
-  uint64_t rp[64], rs[64], rw[64], tq[64];
+  WarpQueues wq[kWarps];
 };
 
 template <typename T>
@@ -245,15 +241,15 @@ __device__ __forceinline__ uint32_t find_request(const BatchReq* reqs, uint32_t 
   return lo;
 }
 
-// One run: tiles [t0, t1) of request r, by the whole CTA, class known at
-// compile time.  Returns the consumer's ring cursor; sets sh.abort if a
-// bounded wait gave up.
+// One session: tiles [t0, t1) of request r, by the whole CTA, class known
+// at compile time.  On return this thread's warp has finished its outputs
+// of the session (the warps have not synchronised).
 #ifndef ZIG_BATCH_RUN_ATTR
 #define ZIG_BATCH_RUN_ATTR __forceinline__
 #endif
 template <int DIST, typename T>
-__device__ ZIG_BATCH_RUN_ATTR unsigned batch_run(BatchCtaState& sh, const BatchReq* reqs, uint32_t r,
-                                           uint64_t t0, uint64_t t1, Limits lim, unsigned hd) {
+__device__ ZIG_BATCH_RUN_ATTR void batch_run(BatchCtaState& sh, const BatchReq* reqs, uint32_t r,
+                                           uint64_t t0, uint64_t t1, Limits lim) {
   const BatchReq& q = reqs[r];
   BatchSink<DIST, T> sink;
   sink.out = (T*)q.out;
@@ -262,10 +258,8 @@ __device__ ZIG_BATCH_RUN_ATTR unsigned batch_run(BatchCtaState& sh, const BatchR
   sink.b = sizeof(T) == 8 ? (T)q.b64 : (T)q.b32;
   const uint64_t seed = q.seed, tile0 = q.tile0;
   const RoundKeys rk = device_keys(seed);
-  if (!gen_tiles<DIST, T, GenShape<T>, 0>(sh, sink, batch_sx<T>(sh, DIST), q.n, q.head, q.nvec, seed, q.offset,
-                          rk, lim, t0 - tile0, t1 - tile0, 1, t0 == tile0, hd))
-    sh.abort = 1u;
-  return hd;
+  gen_tiles<DIST, T, GenShape<T>, 0>(sh, sink, batch_sx<T>(sh, DIST), q.n, q.head, q.nvec, seed,
+                                     q.offset, rk, lim, t0 - tile0, t1 - tile0, 1, t0 == tile0);
 }
 
 __device__ __forceinline__ unsigned smid() {
@@ -319,7 +313,7 @@ __device__ bool batch_claim(BatchRange* rng, unsigned nr, unsigned home, unsigne
 }
 
 #ifndef ZIG_BATCH_MINBLOCKS
-#define ZIG_BATCH_MINBLOCKS 4
+#define ZIG_BATCH_MINBLOCKS 2
 #endif
 __global__ void __launch_bounds__(kThreads, ZIG_BATCH_MINBLOCKS)
     batch_kernel(BatchReq* reqs, BatchHeader* hdr, Limits lim) {
@@ -333,16 +327,11 @@ __global__ void __launch_bounds__(kThreads, ZIG_BATCH_MINBLOCKS)
       sh.sX32[d][k] = g_tab[d].X32[k];
     }
   }
-  for (int k = tid; k < kRing; k += kThreads) sh.ring[k] = kEmpty;
   const uint32_t count = hdr->count;
   BatchRange* rng = (BatchRange*)((char*)hdr + batch_ranges_offset(count));
   unsigned home = 0, scan = 0;
   uint32_t r = 0;  // thread 0: request of the last session
   if (tid == 0) {
-    sh.tail = 0;
-    sh.head = 0;
-    sh.done = 0;
-    sh.abort = 0;
     home = batch_home(hdr, (int*)((char*)hdr + batch_smmap_offset(count)));
     uint64_t pos = 0, end = 0;
     if (batch_claim(rng, hdr->nranges, home, scan, pos, end)) r = find_request(reqs, count, pos);
@@ -350,7 +339,6 @@ __global__ void __launch_bounds__(kThreads, ZIG_BATCH_MINBLOCKS)
     s_end = end;
     s_req = r;
   }
-  unsigned hd = 0;
   __syncthreads();
   for (;;) {
     const uint64_t t = s_pos, end = s_end;
@@ -359,10 +347,10 @@ __global__ void __launch_bounds__(kThreads, ZIG_BATCH_MINBLOCKS)
     const uint64_t rend = reqs[q].tile0 + reqs[q].ntiles;
     const uint64_t t1 = rend < end ? rend : end;
     switch (reqs[q].cls) {
-      case 0: hd = batch_run<ZIG_EXP, float>(sh, reqs, q, t, t1, lim, hd); break;
-      case 1: hd = batch_run<ZIG_NORMAL, float>(sh, reqs, q, t, t1, lim, hd); break;
-      case 2: hd = batch_run<ZIG_EXP, double>(sh, reqs, q, t, t1, lim, hd); break;
-      default: hd = batch_run<ZIG_NORMAL, double>(sh, reqs, q, t, t1, lim, hd); break;
+      case 0: batch_run<ZIG_EXP, float>(sh, reqs, q, t, t1, lim); break;
+      case 1: batch_run<ZIG_NORMAL, float>(sh, reqs, q, t, t1, lim); break;
+      case 2: batch_run<ZIG_EXP, double>(sh, reqs, q, t, t1, lim); break;
+      default: batch_run<ZIG_NORMAL, double>(sh, reqs, q, t, t1, lim); break;
     }
     __threadfence();  // this thread's outputs of the session, before it counts
     __syncthreads();
@@ -386,7 +374,6 @@ __global__ void __launch_bounds__(kThreads, ZIG_BATCH_MINBLOCKS)
       s_req = r;
     }
     __syncthreads();
-    if (sh.abort) break;
   }
 }
 

@@ -5,20 +5,16 @@
 // every output without divergence: the Philox block, the word split, one
 // shared-memory lookup of X_i, one fused multiply-add and a vector store.
 //
-// Each CTA is warp-specialised.  Seven producer warps run only steps 1-2:
-// a draw whose layer index is not below L_max is stored like the others
-// and its position is published in a CTA shared-memory ring.  One consumer
-// warp takes positions 32 at a time and runs the rest of the algorithm for
-// them in stages, so the 32 lanes of a batch execute the same step:
+// Every warp runs steps 1-2 for its outputs: a draw whose layer index is
+// not below L_max is stored like the others (a placeholder) and its
+// position is appended to the warp's queue in shared memory.  Whenever the
+// queue holds 32 positions the warp runs the rest of the algorithm for
+// them in stages, so the 32 lanes execute the same step:
 //   stage 1: steps 3-7 (alias pick, first attempt in the overhang box);
 //   stage 2: one more attempt for each rejected draw (step 8 keeps j);
 //   stage 3: tail draws, through the complete sampler of zig_device.cuh.
-// Its results overwrite the producer's placeholder values.  The producers'
-// code holds no fringe logic and no calls, so it runs without spills at the
-// register budget that four CTAs per SM allow.
-//
-// Every wait is bounded by %globaltimer; a wait that gives up records a
-// device status bit and the kernel returns.
+// Its results overwrite the placeholders.  A warp drains its queues (with
+// partial stages) once its tiles are done.  No warp waits for another.
 //
 // Compiled with --fmad=false: every fused multiply-add is written as one;
 // everything else rounds per operation, as the algorithm's readings state.
@@ -73,7 +69,7 @@ struct VecStore<float, 8> {
 
 // Launch shape (overridable at build time for tuning sweeps).
 #ifndef ZIG_GEN_MINBLOCKS
-#define ZIG_GEN_MINBLOCKS 4
+#define ZIG_GEN_MINBLOCKS 3
 #endif
 #ifndef ZIG_GEN_V64
 #define ZIG_GEN_V64 4
@@ -85,18 +81,15 @@ struct VecStore<float, 8> {
 #define ZIG_GEN_V32 8
 #endif
 #ifndef ZIG_GEN_R32
-#define ZIG_GEN_R32 2
+#define ZIG_GEN_R32 4
 #endif
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kProducerWarps = kWarps - 1;
-constexpr int kPThreads = kProducerWarps * 32;  // producer threads per CTA
-constexpr int kRing = 2048;                     // fringe ring slots per CTA
-constexpr uint64_t kEmpty = ~0ull;              // a free ring slot
-constexpr uint64_t kWholeTag = 1ull << 63;      // position needs the whole sampler
-constexpr unsigned long long kWaitLimitNs = 20ull * 1000ull * 1000ull * 1000ull;
-constexpr unsigned kWaitBit = 1u << 9;          // status bit: a wait gave up
+constexpr int kPThreads = kThreads;          // threads making outputs per CTA (all)
+constexpr int kQueue = 64;                   // fringe queue slots per warp
+constexpr uint64_t kWholeTag = 1ull << 63;   // position needs the whole sampler
+constexpr unsigned kWaitBit = 1u << 9;       // status bit: a bounded wait gave up
 
 // V elements per vector store, R vector stores per producer thread per tile.
 // A generation shape: V-element vectors (one vector store each), R vectors
@@ -118,10 +111,10 @@ template <>
 struct GenShape<float> : Shape<ZIG_GEN_V32, ZIG_GEN_R32, ZIG_GEN_MINBLOCKS> {};
 
 // Default shapes of packed keying: a Philox block makes 2 FP64 / 4 FP32
-// outputs, so a thread makes more outputs per tile (FP32: 32) to spread the
-// tile's fixed costs; measured on GB300 against R = 1, 2 and V = 4.
+// outputs, so an FP32 thread makes 64 outputs per tile to spread the tile's
+// fixed costs (measured on GB300 against R = 2 and 4).
 #ifndef ZIG_PACKED_R32
-#define ZIG_PACKED_R32 4
+#define ZIG_PACKED_R32 8
 #endif
 template <typename T>
 struct PackedShape;
@@ -193,68 +186,25 @@ __device__ __forceinline__ RoundKeys device_keys(uint64_t seed) {
   return rk;
 }
 
+// One warp's fringe queues in shared memory: new positions (q), rejected
+// attempts waiting for the next one (rp: position, rs: state, rw: saved
+// word) and tail draws (tq), with their lengths (warp-uniform).
+struct WarpQueues {
+  uint64_t q[kQueue];
+  uint64_t rp[kQueue], rs[kQueue], rw[kQueue], tq[kQueue];
+  int nq, nr, nt;
+};
+
 // Shared state of one CTA.
 template <typename T>
 struct CtaState {
   T sX[256];
-  uint64_t ring[kRing];
-  unsigned tail;  // ring slots reserved by producers (monotone)
-  unsigned head;  // ring slots released by the consumer (monotone)
-  unsigned done;  // producer warps finished
-  // consumer's stage queues: retries (position, state, saved word), tails
-  uint64_t rp[64], rs[64], rw[64], tq[64];
+  WarpQueues wq[kWarps];
 };
 
-// Producer: publish `cnt` positions per lane (pos(k), k < cnt) in the ring
-// as one warp-wide reservation.  Lane 0 reserves the warp's slots with one
-// atomic and, only if the consumer has not yet freed them, waits (bounded);
-// since a reservation never exceeds the ring, the oldest reserved slots can
-// always be written, so waits end.  A lane's own vector stores come before
-// its fence, which comes before its ring writes, so the consumer's later
-// patch of the same address is ordered after them.  Returns false if the
-// wait gave up.
-template <typename State, typename PosFn>
-__device__ __forceinline__ bool publish(State& sh, int cnt, PosFn pos) {
-  const int lane = threadIdx.x & 31;
-  int incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-  unsigned base = 0;
-  int wait = 0;
-  if (lane == 0) {
-    base = atomicAdd(&sh.tail, (unsigned)total);
-    wait = (int)(base + (unsigned)total - ld_volatile(&sh.head)) > kRing;
-  }
-  base = __shfl_sync(0xFFFFFFFFu, base, 0);
-  if (__shfl_sync(0xFFFFFFFFu, wait, 0)) {
-    const unsigned long long t0 = globaltimer();
-    for (;;) {
-      __nanosleep(128);
-      if (lane == 0) {
-        const bool full = (int)(base + (unsigned)total - ld_volatile(&sh.head)) > kRing;
-        wait = !full ? 0 : (globaltimer() - t0 > kWaitLimitNs ? 2 : 1);
-      }
-      wait = __shfl_sync(0xFFFFFFFFu, wait, 0);
-      if (wait == 0) break;
-      if (wait == 2) {
-        if (lane == 0) atomicOr(&g_status, kWaitBit);
-        return false;
-      }
-    }
-  }
-  __threadfence_block();
-  unsigned slot = base + (unsigned)(incl - cnt);
-  for (int k = 0; k < cnt; ++k) sh.ring[(slot++) % kRing] = pos(k);
-  return true;
-}
-
-// Where values go.  A sink receives the producers' vectors (vec, with the
-// bits of the outputs still to be patched by the consumer), a per-tile
-// notification, and the consumer's final values (put).
+// Where values go.  A sink receives the vectors of steps 1-2 (vec, with the
+// bits of the outputs the fringe stages will still patch), a per-tile
+// notification, and the fringe stages' final values (put).
 //
 // StoreSink: materialise into out[0, n); vector vi starts at element
 // head + vi V.
@@ -290,7 +240,7 @@ __device__ __forceinline__ int hist_bin(double x) {
 // x^3, x^4 (FP32 values in FP32 over one tile, then added to FP64
 // accumulators; FP64 values in FP64) and counts the value in the CTA's
 // shared-memory histogram.  Outputs still to be patched are skipped here and
-// counted when the consumer puts their final value.
+// counted when the fringe stages put their final value.
 template <typename T>
 struct MomentSink {
   unsigned* hist;  // CTA shared histogram, kBins entries
@@ -337,8 +287,7 @@ __device__ __forceinline__ void put_signed(Sink& sink, uint64_t p, T x, bool neg
   sink.put(p, (DIST == ZIG_NORMAL && negative) ? -x : x);
 }
 
-// Consumer queue lengths (warp-uniform), retries in the low half, tails in
-// the high half.
+// Fringe queue lengths (warp-uniform): retries and tails.
 struct SideCounts {
   int retry, tail;
 };
@@ -461,7 +410,7 @@ __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const R
   }
 }
 
-// Consumer: run the retry and tail stages while they hold `need` or more
+// Run the retry and tail stages while they hold `need` or more
 // entries (at most 32 per batch).  Each side queue holds fewer than 32
 // entries before a stage-1 batch, so it stays within its 64 slots.
 template <int DIST, typename T, int KEY, typename Sink, typename State>
@@ -494,6 +443,15 @@ __device__ __forceinline__ void side_stages(Sink& sink, uint64_t seed, uint64_t 
   }
 }
 
+// Mask of a thread's outputs in one tile whose layer index is not below
+// L_max (bit r V + k for output k of vector r): 32 or 64 bits.
+template <int S>
+using FringeMask = typename std::conditional<(S <= 32), unsigned, unsigned long long>::type;
+__device__ __forceinline__ int mask_popc(unsigned m) { return __popc(m); }
+__device__ __forceinline__ int mask_popc(unsigned long long m) { return __popcll(m); }
+__device__ __forceinline__ int mask_ffs(unsigned m) { return __ffs(m); }
+__device__ __forceinline__ int mask_ffs(unsigned long long m) { return __ffsll(m); }
+
 #ifndef ZIG_GEN_UNROLL_R
 #define ZIG_GEN_UNROLL_R 1
 #endif
@@ -511,11 +469,12 @@ constexpr int kPackedUnrollR = ZIG_PACKED_UNROLL_R;
 // vector lies inside the output (else vector r exists only if
 // v0 + r kPThreads < nvec).
 template <int DIST, typename T, typename Shp, bool NOWRAP, typename Sink>
-__device__ __forceinline__ unsigned producer_tile(Sink& sink, uint64_t g0, uint64_t v0,
-                                                  uint64_t nvec, bool full, const RoundKeys& rk,
-                                                  const T* sX, uint32_t L) {
+__device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
+    Sink& sink, uint64_t g0, uint64_t v0, uint64_t nvec, bool full, const RoundKeys& rk,
+    const T* sX, uint32_t L) {
   constexpr int V = Shp::V, R = Shp::R;
-  unsigned fm = 0;
+  static_assert(V * R <= 64, "at most 64 outputs per thread and tile");
+  FringeMask<V * R> fm = 0;
   const RunState run(g0, rk);
 #pragma unroll kUnrollR
   for (int r = 0; r < R; ++r) {
@@ -531,7 +490,7 @@ __device__ __forceinline__ unsigned producer_tile(Sink& sink, uint64_t g0, uint6
     const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
     if (full || vi < nvec) {
       sink.template vec<V>(vi, v, f);
-      fm |= f << (r * V);
+      fm |= (FringeMask<V * R>)f << (r * V);
     }
   }
   sink.tile_end();
@@ -544,14 +503,14 @@ __device__ __forceinline__ unsigned producer_tile(Sink& sink, uint64_t g0, uint6
 // multiple of P and the run's block counters do not wrap their low word;
 // MODE 1: aligned, with wrap; MODE 2: not aligned (one block per output).
 template <int DIST, typename T, typename Shp, int MODE, typename Sink>
-__device__ __forceinline__ unsigned producer_tile_packed(Sink& sink, uint64_t g0, uint64_t v0,
-                                                         uint64_t nvec, bool full,
-                                                         const RoundKeys& rk, const T* sX,
-                                                         uint32_t L) {
+__device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
+    Sink& sink, uint64_t g0, uint64_t v0, uint64_t nvec, bool full, const RoundKeys& rk,
+    const T* sX, uint32_t L) {
   constexpr int V = Shp::V, R = Shp::R;
   constexpr int P = sizeof(T) == 8 ? 2 : 4, SH = sizeof(T) == 8 ? 1 : 2, B = V / P;
   static_assert(V % P == 0, "a vector holds whole blocks");
-  unsigned fm = 0;
+  static_assert(V * R <= 64, "at most 64 outputs per thread and tile");
+  FringeMask<V * R> fm = 0;
   const uint64_t h0 = g0 >> SH;
   const RunState run(h0, rk);
 #pragma unroll kPackedUnrollR
@@ -589,7 +548,7 @@ __device__ __forceinline__ unsigned producer_tile_packed(Sink& sink, uint64_t g0
     const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
     if (full || vi < nvec) {
       sink.template vec<V>(vi, v, f);
-      fm |= f << (r * V);
+      fm |= (FringeMask<V * R>)f << (r * V);
     }
   }
   sink.tile_end();
@@ -613,127 +572,135 @@ struct ReduceOut {
   unsigned* ticket;               // workspace: CTAs finished (zero before launch)
 };
 
+// Fringe work of one warp: stage 1 on its queued positions, 32 at a time,
+// while 32 or more are queued (all of them when draining), with the retry
+// and tail stages run whenever 32 or more entries wait (all when draining).
+// The sink travels by value so that the caller keeps its copy in registers.
+#ifndef ZIG_FRINGE_ATTR
+#define ZIG_FRINGE_ATTR __forceinline__
+#endif
+template <int DIST, typename T, int KEY, typename Sink>
+__device__ ZIG_FRINGE_ATTR Sink fringe_work(Sink sink, WarpQueues& wq, uint64_t seed,
+                                            uint64_t offset, Limits lim, bool drain) {
+  const int lane = threadIdx.x & 31;
+  const RoundKeys rk = device_keys(seed);
+  SideCounts c{wq.nr, wq.nt};
+  int nq = wq.nq;
+  __syncwarp();  // every lane's placeholder stores come before the fixes
+  while (nq >= 32 || (drain && nq > 0)) {
+    const int take = nq < 32 ? nq : 32;
+    const bool active = lane < take;
+    const uint64_t item = active ? wq.q[nq - take + lane] : 0;
+    nq -= take;
+    __syncwarp();
+    stage_new<DIST, T, ~kWholeTag, KEY>(sink, offset, rk, lim, active, item, wq, c);
+    __syncwarp();
+    side_stages<DIST, T, KEY>(sink, seed, offset, rk, lim, 32, wq, c);
+  }
+  if (drain) side_stages<DIST, T, KEY>(sink, seed, offset, rk, lim, 1, wq, c);
+  __syncwarp();
+  if (lane == 0) {
+    wq.nq = nq;
+    wq.nr = c.retry;
+    wq.nt = c.tail;
+  }
+  __syncwarp();
+  return sink;
+}
+
 // One CTA's share of a generation over outputs [0, n): a head of < V
 // elements up to the first V-element-aligned address, nvec aligned
 // V-vectors, then a tail of < V elements.  Tile t covers vectors
-// [t kTile, (t + 1) kTile); producer thread pt makes vectors
-// t kTile + r kPThreads + pt, r < R.  This CTA takes tiles tile, tile + step,
-// ... below tile_end; if `ends`, its warp 0 also publishes the head and tail
-// elements for the whole sampler.  Producer warps return after publishing
-// their last tile (counting themselves in sh.done); the consumer warp
-// returns once every published item has its final value, with sh.done
-// reset to zero and its ring cursor hd advanced past the items.  Returns
-// false if a bounded wait gave up.
+// [t kTile, (t + 1) kTile); thread pt makes vectors t kTile + r kPThreads +
+// pt, r < R.  This CTA takes tiles tile, tile + step, ... below tile_end;
+// if `ends`, its warp 0 also queues the head and tail elements for the
+// whole sampler.  Each warp queues the positions of its draws whose layer
+// index is not below L_max, runs the fringe stages for every 32 of them and
+// drains its queues before returning; on return every output of the CTA's
+// tiles has its final value (the warps have not synchronised).
 template <int DIST, typename T, typename Shp, int KEY, typename Sink, typename State>
-__device__ __forceinline__ bool gen_tiles(State& sh, Sink& sink, const T* sX, uint64_t n,
+__device__ __forceinline__ void gen_tiles(State& sh, Sink& sink, const T* sX, uint64_t n,
                                           uint64_t head, uint64_t nvec, uint64_t seed,
                                           uint64_t offset, const RoundKeys& rk, Limits lim,
                                           uint64_t tile, uint64_t tile_end, uint64_t step,
-                                          bool ends, unsigned& hd) {
-  constexpr int V = Shp::V, R = Shp::R, S = V * R;
+                                          bool ends) {
+  constexpr int V = Shp::V, R = Shp::R;
   constexpr int kTile = kPThreads * R;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  bool ok = true;
-  if (tid < kPThreads) {
-    // ---------------- producer warps: steps 1-2 only ----------------
-    const uint32_t L = (uint32_t)g_tab[DIST].L;
-    const uint64_t body_end = head + nvec * V;
-    if (ends && tid < 32) {
-      // head and tail elements (fewer than V each) take the whole sampler
-      const int hc = (uint64_t)lane < head ? 1 : 0;
-      const int tc = (uint64_t)lane < n - body_end ? 1 : 0;
-      ok = publish(sh, hc + tc, [&](int k) {
-        return kWholeTag | ((k == 0 && hc) ? (uint64_t)lane : body_end + (uint64_t)lane);
-      });
+  WarpQueues& wq = sh.wq[tid >> 5];
+  const uint32_t L = (uint32_t)g_tab[DIST].L;
+  const uint64_t body_end = head + nvec * V;
+  {
+    // head and tail elements (fewer than V each) take the whole sampler
+    const int hc = ends && tid < 32 && (uint64_t)lane < head ? 1 : 0;
+    const int tc = ends && tid < 32 && (uint64_t)lane < n - body_end ? 1 : 0;
+    const int cnt = hc + tc;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += y;
     }
-    constexpr uint32_t kSpan = (uint32_t)((R - 1) * kPThreads * V + (V - 1));
-    static_assert(32 * S <= kRing, "a warp's reservation must fit the ring");
-    for (; ok && tile < tile_end; tile += step) {
-      const uint64_t v0 = tile * kTile + (uint64_t)tid;  // this thread's first vector
-      const uint64_t p0 = head + v0 * V;                   // and its first position
-      const uint64_t g0 = offset + p0;
-      const bool full = (tile + 1) * kTile <= nvec;
-      unsigned fm;  // outputs of this thread whose layer index is >= L_max
-      if (KEY == 0) {
-        if ((uint32_t)g0 <= 0xFFFFFFFFu - kSpan)
-          fm = producer_tile<DIST, T, Shp, true>(sink, g0, v0, nvec, full, rk, sX, L);
-        else
-          fm = producer_tile<DIST, T, Shp, false>(sink, g0, v0, nvec, full, rk, sX, L);
-      } else {
-        constexpr int P = sizeof(T) == 8 ? 2 : 4, SH = sizeof(T) == 8 ? 1 : 2;
-        constexpr uint32_t kSpanB = (uint32_t)((R - 1) * kPThreads * (V / P) + (V / P - 1));
-        if (g0 % P != 0)
-          fm = producer_tile_packed<DIST, T, Shp, 2>(sink, g0, v0, nvec, full, rk, sX, L);
-        else if ((uint32_t)(g0 >> SH) <= 0xFFFFFFFFu - kSpanB)
-          fm = producer_tile_packed<DIST, T, Shp, 0>(sink, g0, v0, nvec, full, rk, sX, L);
-        else
-          fm = producer_tile_packed<DIST, T, Shp, 1>(sink, g0, v0, nvec, full, rk, sX, L);
-      }
-      if (__any_sync(0xFFFFFFFFu, fm != 0)) {
-        const unsigned fmask = fm;
-        ok = publish(sh, __popc(fmask), [&](int k) {
-          unsigned m = fmask;
-          for (int q = 0; q < k; ++q) m &= m - 1u;  // k-th set bit
-          const int s = __ffs(m) - 1;
-          return p0 + (uint64_t)((s / V) * (kPThreads * V) + (s % V));
-        });
-      }
+    int slot = incl - cnt;
+    if (hc) wq.q[slot++] = kWholeTag | (uint64_t)lane;
+    if (tc) wq.q[slot] = kWholeTag | (body_end + (uint64_t)lane);
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (lane == 0) {
+      wq.nq = total;
+      wq.nr = 0;
+      wq.nt = 0;
     }
     __syncwarp();
-    __threadfence_block();  // every lane's ring writes before the count
-    if (lane == 0) atomicAdd(&sh.done, 1u);
-  } else {
-    // ---------------- consumer warp: steps 3-8 in stages ----------------
-    SideCounts c{0, 0};
-    unsigned long long t0 = globaltimer();
-    for (;;) {
-      const uint64_t item = ld_volatile(&sh.ring[(hd + (unsigned)lane) % kRing]);
-      const unsigned ready = __ballot_sync(0xFFFFFFFFu, item != kEmpty);
-      const int avail = ready == 0xFFFFFFFFu ? 32 : __ffs(~ready) - 1;
-      bool last = false;
-      if (avail < 32) {
-        // lane 0 decides for the warp: done, or keep waiting, or give up
-        int state = 0;
-        if (lane == 0) {
-          if (ld_volatile(&sh.done) == (unsigned)kProducerWarps) {
-            __threadfence_block();
-            // every reserved slot is written once the producers are done
-            if (hd + (unsigned)avail == ld_volatile(&sh.tail)) state = 1;
-          }
-          if (state == 0 && globaltimer() - t0 > kWaitLimitNs) state = 2;
-        }
-        state = __shfl_sync(0xFFFFFFFFu, state, 0);
-        if (state == 2) {
-          if (lane == 0) atomicOr(&g_status, kWaitBit);
-          ok = false;
-          break;
-        }
-        if (state == 0) {
-          __nanosleep(1000);
-          continue;
-        }
-        last = true;
-      }
-      __threadfence_block();  // the producers' stores come before our patches
-      const bool active = lane < avail;
-      if (active) sh.ring[(hd + (unsigned)lane) % kRing] = kEmpty;
-      hd += (unsigned)avail;
-      __threadfence_block();
-      __syncwarp();
-      if (lane == 0) *(volatile unsigned*)&sh.head = hd;
-      stage_new<DIST, T, ~kWholeTag, KEY>(sink, offset, rk, lim, active, active ? item : 0, sh,
-                                          c);
-      __syncwarp();
-      side_stages<DIST, T, KEY>(sink, seed, offset, rk, lim, last ? 1 : 32, sh, c);
-      if (last) break;
-      t0 = globaltimer();
-    }
-    // the producers have all counted themselves; none touches sh.done again
-    // before the caller's next barrier
-    if (lane == 0) sh.done = 0u;
   }
-  return ok;
+  constexpr uint32_t kSpan = (uint32_t)((R - 1) * kPThreads * V + (V - 1));
+  for (; tile < tile_end; tile += step) {
+    const uint64_t v0 = tile * kTile + (uint64_t)tid;  // this thread's first vector
+    const uint64_t p0 = head + v0 * V;                   // and its first position
+    const uint64_t g0 = offset + p0;
+    const bool full = (tile + 1) * kTile <= nvec;
+    FringeMask<V * R> fm;  // outputs of this thread whose layer index is >= L_max
+    if (KEY == 0) {
+      if ((uint32_t)g0 <= 0xFFFFFFFFu - kSpan)
+        fm = producer_tile<DIST, T, Shp, true>(sink, g0, v0, nvec, full, rk, sX, L);
+      else
+        fm = producer_tile<DIST, T, Shp, false>(sink, g0, v0, nvec, full, rk, sX, L);
+    } else {
+      constexpr int P = sizeof(T) == 8 ? 2 : 4, SH = sizeof(T) == 8 ? 1 : 2;
+      constexpr uint32_t kSpanB = (uint32_t)((R - 1) * kPThreads * (V / P) + (V / P - 1));
+      if (g0 % P != 0)
+        fm = producer_tile_packed<DIST, T, Shp, 2>(sink, g0, v0, nvec, full, rk, sX, L);
+      else if ((uint32_t)(g0 >> SH) <= 0xFFFFFFFFu - kSpanB)
+        fm = producer_tile_packed<DIST, T, Shp, 0>(sink, g0, v0, nvec, full, rk, sX, L);
+      else
+        fm = producer_tile_packed<DIST, T, Shp, 1>(sink, g0, v0, nvec, full, rk, sX, L);
+    }
+    // queue the positions; run the fringe stages whenever 32 are queued
+    FringeMask<V * R> m = fm;
+    while (__any_sync(0xFFFFFFFFu, m != 0)) {
+      const int cnt = mask_popc(m);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      const int nq = wq.nq;  // < 32 here
+      int slot = nq + incl - cnt;
+      while (m != 0 && slot < kQueue) {
+        const int s = mask_ffs(m) - 1;
+        m &= m - 1u;
+        wq.q[slot++] = p0 + (uint64_t)((s / V) * (kPThreads * V) + (s % V));
+      }
+      __syncwarp();
+      const int added = total < kQueue - nq ? total : kQueue - nq;
+      if (lane == 0) wq.nq = nq + added;
+      __syncwarp();
+      if (nq + added >= 32) sink = fringe_work<DIST, T, KEY>(sink, wq, seed, offset, lim, false);
+    }
+  }
+  sink = fringe_work<DIST, T, KEY>(sink, wq, seed, offset, lim, true);
 }
 
 // One launch covers outputs [0, n) (layout as in gen_tiles); CTA b takes
@@ -749,21 +716,14 @@ __global__ void __launch_bounds__(kThreads, Shp::MB)
 
   const int tid = threadIdx.x;
   for (int k = tid; k < 256; k += kThreads) sh.sX[k] = Prec<T>::X(g_tab[DIST], k);
-  for (int k = tid; k < kRing; k += kThreads) sh.ring[k] = kEmpty;
   if (Sink::kReduce)
     for (int k = tid; k < kBins; k += kThreads) shist[k] = 0u;
-  if (tid == 0) {
-    sh.tail = 0;
-    sh.head = 0;
-    sh.done = 0;
-  }
   if constexpr (Sink::kReduce) sink.init(shist);
   __syncthreads();
 
   const uint64_t ntiles = (nvec + kTile - 1) / kTile;
-  unsigned hd = 0;
   gen_tiles<DIST, T, Shp, KEY>(sh, sink, sh.sX, n, head, nvec, seed, offset, rk, lim,
-                               blockIdx.x, ntiles, gridDim.x, blockIdx.x == 0, hd);
+                               blockIdx.x, ntiles, gridDim.x, blockIdx.x == 0);
 
   if constexpr (Sink::kReduce) {
     // CTA partials in thread order, then the CTA's histogram into the
@@ -933,22 +893,23 @@ zig_status launch_gen(void* out, uint64_t n, uint64_t seed, uint64_t offset,
 }
 
 // The autotuner's candidate shapes per precision (index 0 is the default).
-// FP64: 16- or 32-byte vectors, 8-32 outputs per thread and tile, 3-4
-// CTAs per SM; FP32 likewise with 16- or 32-byte vectors.
+// FP64: 16- or 32-byte vectors, 8-16 outputs per thread and tile, register
+// budgets for 2-4 CTAs per SM; FP32 likewise with 16- or 32-byte vectors
+// and 16-64 outputs per thread and tile.
 constexpr int kVariants = 5;
 template <typename T>
 struct Variants;
 template <>
 struct Variants<double> {
-  static constexpr int V[kVariants] = {GenShape<double>::V, 4, 2, 4, 2};
-  static constexpr int R[kVariants] = {GenShape<double>::R, 2, 4, 4, 8};
-  static constexpr int MB[kVariants] = {GenShape<double>::MB, 4, 4, 3, 4};
+  static constexpr int V[kVariants] = {GenShape<double>::V, 4, 2, 4, 4};
+  static constexpr int R[kVariants] = {GenShape<double>::R, 2, 4, 4, 4};
+  static constexpr int MB[kVariants] = {GenShape<double>::MB, 3, 3, 4, 2};
 };
 template <>
 struct Variants<float> {
-  static constexpr int V[kVariants] = {GenShape<float>::V, 8, 4, 8, 4};
-  static constexpr int R[kVariants] = {GenShape<float>::R, 1, 4, 2, 2};
-  static constexpr int MB[kVariants] = {GenShape<float>::MB, 4, 4, 3, 4};
+  static constexpr int V[kVariants] = {GenShape<float>::V, 8, 4, 8, 8};
+  static constexpr int R[kVariants] = {GenShape<float>::R, 2, 4, 4, 8};
+  static constexpr int MB[kVariants] = {GenShape<float>::MB, 3, 3, 2, 3};
 };
 
 template <int DIST, typename T, int K>

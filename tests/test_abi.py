@@ -106,8 +106,8 @@ def test_tune_candidates(zig):
     assert len(f64) == 5 and len(f32) == 5
     # the defaults come first; all shapes distinct; outputs per thread and
     # tile fit a warp's ring reservation (32 V R <= 2048)
-    assert (f64[0]["V"], f64[0]["R"], f64[0]["min_blocks"]) == (4, 4, 4)
-    assert (f32[0]["V"], f32[0]["R"], f32[0]["min_blocks"]) == (8, 2, 4)
+    assert (f64[0]["V"], f64[0]["R"], f64[0]["min_blocks"]) == (4, 4, 3)
+    assert (f32[0]["V"], f32[0]["R"], f32[0]["min_blocks"]) == (8, 4, 3)
     for c in (f64, f32):
         assert len({(e["V"], e["R"], e["min_blocks"]) for e in c}) == len(c)
         assert all(32 * e["V"] * e["R"] <= 2048 for e in c)
@@ -121,13 +121,15 @@ def test_tune_cache_roundtrip(zig, tmp_path):
     import json
 
     src = tmp_path / "in.jsonl"
+    c64, c32 = zig.zig_tune_candidates(1), zig.zig_tune_candidates(0)
+    a1, a2, b1 = c64[1], c64[2], c32[1]
     lines = [
-        {"device": "test-device-A", "sms": 8, "dist": "normal", "dtype": "f64", "V": 4, "R": 2,
-         "min_blocks": 4, "blocks_per_sm": 3, "gsamples_s": 1.5},
-        {"device": "test-device-A", "sms": 8, "dist": "normal", "dtype": "f64", "V": 2, "R": 4,
-         "min_blocks": 4, "blocks_per_sm": 2, "gsamples_s": 2.5},
-        {"device": "test \"quoted\" B", "sms": 9, "dist": "exp", "dtype": "f32", "V": 8, "R": 1,
-         "min_blocks": 4, "blocks_per_sm": 0, "gsamples_s": 3.0},
+        {"device": "test-device-A", "sms": 8, "dist": "normal", "dtype": "f64", "V": a1["V"],
+         "R": a1["R"], "min_blocks": a1["min_blocks"], "blocks_per_sm": 3, "gsamples_s": 1.5},
+        {"device": "test-device-A", "sms": 8, "dist": "normal", "dtype": "f64", "V": a2["V"],
+         "R": a2["R"], "min_blocks": a2["min_blocks"], "blocks_per_sm": 2, "gsamples_s": 2.5},
+        {"device": "test \"quoted\" B", "sms": 9, "dist": "exp", "dtype": "f32", "V": b1["V"],
+         "R": b1["R"], "min_blocks": b1["min_blocks"], "blocks_per_sm": 0, "gsamples_s": 3.0},
         # no such candidate shape, unknown dist, missing field: skipped
         {"device": "test-device-A", "sms": 8, "dist": "exp", "dtype": "f64", "V": 3, "R": 3,
          "min_blocks": 4, "blocks_per_sm": 1},
@@ -144,7 +146,8 @@ def test_tune_cache_roundtrip(zig, tmp_path):
             if g["device"].startswith("test")}
     assert set(mine) == {("test-device-A", 8, "normal", "f64"), ('test "quoted" B', 9, "exp", "f32")}
     a = mine[("test-device-A", 8, "normal", "f64")]
-    assert (a["V"], a["R"], a["min_blocks"], a["blocks_per_sm"]) == (2, 4, 4, 2)
+    assert (a["V"], a["R"], a["min_blocks"], a["blocks_per_sm"]) == (
+        a2["V"], a2["R"], a2["min_blocks"], 2)
     assert a["gsamples_s"] == pytest.approx(2.5)
     with pytest.raises(zig.ZigError):
         zig.zig_tune_load(str(tmp_path / "missing.jsonl"))
