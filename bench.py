@@ -191,11 +191,13 @@ def run_reference(args):
     value = per * args.steps / dt / 1e9
     sample = f"{per} counters per step of {args.workload} (fresh counters each step)"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if c["dtype"] == W.F64 else "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n_per_step": per, "seed": W.SEED},
+        "config": {"workload": args.workload, "dist": "normal" if c["dist"] else "exponential",
+                   "n_per_step": per, "seed": W.SEED,
+                   "note": "the CPU oracle on the host cores (rank 0 only); no GPU work"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
