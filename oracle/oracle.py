@@ -24,7 +24,7 @@ LIB_OVERRIDE = os.environ.get("ZIG_ORACLE_LIB")
 
 EXP, NORMAL = 0, 1
 F32, F64 = 0, 1
-MAXCOLS = 256
+MAXCOLS = 1024
 
 _lock = threading.Lock()
 _lib = None
@@ -66,7 +66,7 @@ class Tables(ctypes.Structure):
         ("rinv32", ctypes.c_float), ("padf", ctypes.c_float),
         ("q", ctypes.c_uint64 * MAXCOLS),
         ("T", ctypes.c_uint64 * MAXCOLS),
-        ("alias", ctypes.c_uint8 * MAXCOLS),
+        ("alias", ctypes.c_uint16 * MAXCOLS),
     ]
 
     def arr(self, name: str) -> np.ndarray:

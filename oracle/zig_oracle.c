@@ -228,7 +228,7 @@ static void build_alias(orc_tables* t, const q128* A, int nmass) {
     int s = small[hs++];
     int l = large[hl];
     t->T[s] = w[s];
-    t->alias[s] = (uint8_t)l;
+    t->alias[s] = (uint16_t)l;
     w[l] -= (K - w[s]);
     if (w[l] < K) {
       hl++;
@@ -238,19 +238,19 @@ static void build_alias(orc_tables* t, const q128* A, int nmass) {
   while (hl < nl) {
     int l = large[hl++];
     t->T[l] = K;
-    t->alias[l] = (uint8_t)l;
+    t->alias[l] = (uint16_t)l;
   }
   while (hs < ns) {
     int s = small[hs++];
     t->T[s] = K;
-    t->alias[s] = (uint8_t)s;
+    t->alias[s] = (uint16_t)s;
   }
 }
 
 int orc_build_tables(int dist, int ibits, int ubits, int abits,
                      orc_tables* t) {
   if (dist != ORC_EXP && dist != ORC_NORMAL) return 1;
-  if (ibits < 1 || ibits > 8 || ubits < 1 || ubits > 52) return 1;
+  if (ibits < 1 || ibits > 10 || ubits < 1 || ubits > 52) return 1;
   if (abits < 1 || abits > 64 - ibits) return 1;
   memset(t, 0, sizeof(*t));
   t->dist = dist;

@@ -49,7 +49,7 @@ extern "C" {
 enum { ORC_EXP = 0, ORC_NORMAL = 1 };
 enum { ORC_F32 = 0, ORC_F64 = 1 };
 
-#define ORC_MAXCOLS 256
+#define ORC_MAXCOLS 1024
 
 /* Tables for one distribution.  Index conventions (Sec. 2):
  *   layer k = 0..L-1 is the rectangle [0, X_k] x [f_{k-1}, f_k], f_{-1} = 0;
@@ -59,7 +59,8 @@ enum { ORC_F32 = 0, ORC_F64 = 1 };
  * the exact rejection test reads y < exp(-x^2/2). */
 typedef struct orc_tables {
   int32_t dist;   /* ORC_EXP or ORC_NORMAL */
-  int32_t imax;   /* number of equal-area slots (256 at full width) */
+  int32_t imax;   /* number of equal-area slots (256 at full width; 1024 for the
+                     10-bit index variant of Appendix D item 1) */
   int32_t ibits;  /* log2(imax) */
   int32_t L;      /* L_max, layers wholly under P */
   int32_t ubits;  /* bits of U taken from the top of a word (52 full width) */
@@ -82,16 +83,17 @@ typedef struct orc_tables {
   float padf;
   uint64_t q[ORC_MAXCOLS];     /* integer alias weights, sum = imax * 2^abits */
   uint64_t T[ORC_MAXCOLS];     /* alias thresholds in [0, 2^abits] */
-  uint8_t alias[ORC_MAXCOLS];  /* alias targets */
+  uint16_t alias[ORC_MAXCOLS]; /* alias targets */
 } orc_tables;
 
 /* Philox4x32-10 block: out = Philox(ctr, key). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                        uint32_t out[4]);
 
-/* Build tables for dist with imax = 2^ibits slots, U taken from the top
- * ubits of a word, alias thresholds from the top abits.  Full width is
- * (ibits, ubits, abits) = (8, 52, 56).  Returns 0 on success. */
+/* Build tables for dist with imax = 2^ibits slots (ibits <= 10), U taken
+ * from the top ubits of a word, alias thresholds from the top abits.  Full
+ * width is (ibits, ubits, abits) = (8, 52, 56); the 10-bit index variant is
+ * (10, 52, 54).  Returns 0 on success. */
 int orc_build_tables(int dist, int ibits, int ubits, int abits,
                      orc_tables* t);
 

@@ -346,3 +346,24 @@ def test_fp32_tracks_fp64_on_same_counters(orc):
         assert d.max() <= 7.6 * 2.0**-23 + 2.0**-21
         flips = float(np.mean(w64 != w32))
         assert flips < 1e-3
+
+
+@pytest.mark.parametrize("dist,dtype", [(0, 1), (1, 1), (0, 0), (1, 0)])
+def test_distribution_ten_bit_index(orc, dist, dtype):
+    """i_max = 1024 (Appendix D item 1): i from bits 0-9, the normal's sign
+    from bit 10, alias column from bits 0-9 and threshold from bits 10-63;
+    the same laws, and step 2 exits at the rate L_max / 1024."""
+    te, tn = orc.tables(0, 10, 52, 54), orc.tables(1, 10, 52, 54)
+    x, errs, words, _ = orc.fill(dist, dtype, SEED, 0, N_STAT, want_words=True, te=te, tn=tn)
+    assert errs == 0 and np.all(np.isfinite(x))
+    x = x.astype(np.float64)
+    assert stats.kstest(x, _cdf(dist)).pvalue > 1e-4
+    cnt = np.bincount(np.searchsorted(_equiprob_edges(dist), x, side="right"), minlength=1024)
+    chi2 = float(((cnt - N_STAT / 1024) ** 2 / (N_STAT / 1024)).sum())
+    assert abs(chi2 - 1023) < 6 * math.sqrt(2 * 1023), chi2
+    L = (te if dist == 0 else tn).L
+    p = L / 1024
+    rate = float(np.mean(words == 1))
+    assert abs(rate - p) < 5 * math.sqrt(p * (1 - p) / N_STAT)
+    if dist == 1:
+        assert abs(float(np.mean(x > 0)) - 0.5) < 5 * math.sqrt(0.25 / N_STAT)

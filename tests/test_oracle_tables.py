@@ -5,7 +5,9 @@ with something fixed independently of its code: the paper's printed L_max,
 the Lambert-W closed form of the exponential tail point, 40-digit mpmath
 evaluations of the defining equations, numerical quadrature of the overhang
 integrals, brute-force maximisation of the chord gap, and exact integer
-identities of the alias table.
+identities of the alias table.  The structural pins run at both index
+widths: 8 bits (i_max = 256, the paper's tables) and 10 bits (i_max = 1024,
+the variant of Appendix D item 1).
 """
 import math
 
@@ -17,6 +19,8 @@ mp = pytest.importorskip("mpmath")
 mp.mp.dps = 40
 
 IMAX = 256
+# (index bits, alias threshold bits) of the two widths the library builds
+WIDTHS = [(8, 56), (10, 54)]
 
 
 def _P(dist, x):
@@ -66,9 +70,11 @@ def test_tail_point_normal_root(tn):
     assert abs(tn.X[0] - float(x0)) <= _ulp(float(x0))
 
 
+@pytest.mark.parametrize("width", WIDTHS)
 @pytest.mark.parametrize("dist", [0, 1])
-def test_layers_equal_area_residuals(orc, dist):
-    t = orc.tables(dist)
+def test_layers_equal_area_residuals(orc, dist, width):
+    t = orc.tables(dist, width[0], 52, width[1])
+    IMAX = t.imax
     fprev = mp.mpf(0)
     Xprev = None
     for k in range(t.L):
@@ -90,17 +96,18 @@ def test_layers_equal_area_residuals(orc, dist):
         dh = h if dist == 0 else h * X
         assert abs(t.f[k] - h) <= _ulp(float(h)) + dh * _ulp(t.X[k]) / 2, k
         fprev, Xprev = fk, X
-    # No further layer of area 1/256 fits above the last one: max_X of
-    # X (P(X) - f_{L-1}) over [0, X_{L-1}] is below 1/256.
+    # No further layer of area 1/i_max fits above the last one: max_X of
+    # X (P(X) - f_{L-1}) over [0, X_{L-1}] is below 1/i_max.
     xs = np.linspace(0, t.X[t.L - 1], 20001)
     g = max(float(mp.mpf(x) * (_P(dist, x) - fprev)) for x in xs[::50])
     assert g < 1.0 / IMAX
     assert t.X[t.L] == 0.0 and t.f[t.L] == 1.0
 
 
+@pytest.mark.parametrize("width", WIDTHS)
 @pytest.mark.parametrize("dist", [0, 1])
-def test_differences(orc, dist):
-    t = orc.tables(dist)
+def test_differences(orc, dist, width):
+    t = orc.tables(dist, width[0], 52, width[1])
     for j in range(1, t.L + 1):
         ref_dx = t.X[j - 1] - t.X[j]
         assert abs(t.dX[j] - ref_dx) <= _ulp(t.X[j - 1]) + _ulp(t.X[j]) + _ulp(ref_dx), j
@@ -109,9 +116,10 @@ def test_differences(orc, dist):
         assert t.dX[j] > 0 and t.df[j] > 0
 
 
+@pytest.mark.parametrize("width", WIDTHS)
 @pytest.mark.parametrize("dist", [0, 1])
-def test_overhang_masses_quadrature(orc, dist):
-    t = orc.tables(dist)
+def test_overhang_masses_quadrature(orc, dist, width):
+    t = orc.tables(dist, width[0], 52, width[1])
     c = math.sqrt(2 / math.pi)
     dens = (lambda x: math.exp(-x)) if dist == 0 else (lambda x: c * math.exp(-x * x / 2))
     fn = [dens(t.X[k]) for k in range(t.L)] + [dens(0.0)]
@@ -123,10 +131,11 @@ def test_overhang_masses_quadrature(orc, dist):
     assert t.A[0] == pytest.approx(tail, rel=1e-13)
 
 
+@pytest.mark.parametrize("width", WIDTHS)
 @pytest.mark.parametrize("dist", [0, 1])
-def test_total_mass_is_one(orc, dist):
-    t = orc.tables(dist)
-    total = mp.mpf(t.L) / IMAX + mp.fsum(mp.mpf(t.A[j]) for j in range(t.L + 1))
+def test_total_mass_is_one(orc, dist, width):
+    t = orc.tables(dist, width[0], 52, width[1])
+    total = mp.mpf(t.L) / t.imax + mp.fsum(mp.mpf(t.A[j]) for j in range(t.L + 1))
     assert abs(total - 1) < 1e-15
     # The cap above the last layer carries real mass (read R2).
     assert t.A[t.L] > 1e-3
@@ -149,13 +158,15 @@ def test_epsilon_bruteforce(te):
     assert te.tau < 1 - te.eps and te.tau > 1 - te.eps - 1e-11
 
 
+@pytest.mark.parametrize("width", WIDTHS)
 @pytest.mark.parametrize("dist", [0, 1])
-def test_alias_reconstruction_identity(orc, dist):
-    t = orc.tables(dist)
+def test_alias_reconstruction_identity(orc, dist, width):
+    t = orc.tables(dist, width[0], 52, width[1])
+    IMAX = t.imax
     K = 1 << t.abits
-    q = [int(v) for v in t.q]
-    T = [int(v) for v in t.T]
-    al = [int(v) for v in t.alias]
+    q = [int(v) for v in t.q][:IMAX]
+    T = [int(v) for v in t.T][:IMAX]
+    al = [int(v) for v in t.alias][:IMAX]
     assert sum(q) == IMAX * K
     assert all(0 <= T[c] <= K for c in range(IMAX))
     rec = [0] * IMAX
@@ -185,7 +196,7 @@ def test_alias_pick_frequencies(orc, te):
         rng.integers(0, 2, size=n, dtype=np.uint64)
     js = np.array([orc.alias_pick(te, int(w)) for w in words])
     counts = np.bincount(js, minlength=IMAX)
-    p = np.array([int(v) for v in te.q], dtype=float) / 2.0**64
+    p = np.array([int(v) for v in te.q][:IMAX], dtype=float) / 2.0**64
     m = p > 0
     assert counts[~m].sum() == 0
     chi2 = float(((counts[m] - n * p[m]) ** 2 / (n * p[m])).sum())
@@ -193,9 +204,10 @@ def test_alias_pick_frequencies(orc, te):
     assert chi2 < df + 6 * math.sqrt(2 * df)
 
 
-def test_fp32_tables_are_roundings(orc):
+@pytest.mark.parametrize("width", WIDTHS)
+def test_fp32_tables_are_roundings(orc, width):
     for dist in (0, 1):
-        t = orc.tables(dist)
+        t = orc.tables(dist, width[0], 52, width[1])
         for k in range(t.L + 1):
             assert abs(float(t.X32[k]) - t.X[k]) <= np.spacing(np.float32(abs(t.X[k]))) / 2 * (1 + 1e-6)
             assert abs(float(t.f32[k]) - t.f[k]) <= np.spacing(np.float32(abs(t.f[k]))) / 2 * (1 + 1e-6)
@@ -211,3 +223,23 @@ def test_reduced_width_tables(orc):
         total = t.L / 8 + sum(t.A[j] for j in range(t.L + 1))
         assert total == pytest.approx(1.0, abs=1e-14)
         assert sum(int(v) for v in list(t.q)[:8]) == 8 << 12
+
+
+def test_ten_bit_tables_epsilon_and_layers(orc):
+    """i_max = 1024: the chord deviation by brute force (as for 256), and
+    the layer counts and tail points move the way the construction says
+    (more, thinner layers; a tail point further out)."""
+    te = orc.tables(0, 10, 52, 54)
+    tn = orc.tables(1, 10, 52, 54)
+    for j in (1, 2, 100, te.L // 2, te.L):
+        x = np.linspace(te.X[j], te.X[j - 1], 200001)
+        fj, fj1 = math.exp(-te.X[j]), math.exp(-te.X[j - 1])
+        chord = fj + (x - te.X[j]) * (fj1 - fj) / (te.X[j - 1] - te.X[j])
+        assert te.eps_j[j] == pytest.approx(np.max(chord - np.exp(-x)) / (fj - fj1), rel=1e-6)
+    assert te.eps == pytest.approx(max(te.eps_j[j] for j in range(1, te.L + 1)))
+    # X_0 solves X e^-X = 1/1024 (larger root): -W_{-1}(-1/1024)
+    x0 = -mp.lambertw(-mp.mpf(1) / 1024, -1)
+    assert abs(te.X[0] - float(x0)) <= 2 * _ulp(float(x0))
+    t8e, t8n = orc.tables(0), orc.tables(1)
+    assert te.L > 4 * t8e.L - 8 and tn.L > 4 * t8n.L - 8
+    assert te.X[0] > t8e.X[0] and tn.X[0] > t8n.X[0]
