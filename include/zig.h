@@ -118,6 +118,41 @@ typedef struct zig_tables_export {
   uint8_t alias[256];
 } zig_tables_export;
 
+/* The tables at either index width in one layout: i_max = 2^index_bits
+ * columns (index_bits 8: the paper's 256; 10: the 1024 of Appendix D item
+ * 1), arrays indexed as in zig_tables_export.  Alias: column c = w &
+ * (i_max - 1) and threshold t = w >> index_bits give j = c if t < T[c]
+ * else alias[c]; thresholds are on the scale 2^(64 - index_bits). */
+typedef struct zig_tables_ex {
+  int32_t dist;
+  int32_t L;
+  int32_t imax;
+  int32_t index_bits;
+  double X[1025];
+  double f[1025];
+  double dX[1025];
+  double df[1025];
+  double A[1025];
+  double eps;
+  double tau;
+  double rinv;
+  float X32[1025];
+  float f32[1025];
+  float dX32[1025];
+  float df32[1025];
+  float rinv32;
+  float reserved;
+  uint64_t T[1024];
+  uint16_t alias[1024];
+} zig_tables_ex;
+
+/*
+ * zig_export_tables_ex -- copy the host tables of dist at index_bits (8 or
+ * 10) into *h_out.  Builds them if needed (no device is touched).  Returns
+ * ZIG_OK, ZIG_E_INVAL (bad dist, index_bits or NULL) or ZIG_E_TABLE.
+ */
+zig_status zig_export_tables_ex(zig_dist dist, int index_bits, zig_tables_ex* h_out);
+
 /*
  * zig_export_tables -- copy the host tables of dist into *h_out.
  * Builds the host tables if needed (no device is touched).
@@ -293,14 +328,21 @@ typedef enum { ZIG_KEY_INDEX = 0, ZIG_KEY_PACKED = 1 } zig_keying;
 
 /*
  * zig_generate -- zig_exponential (dist ZIG_EXP) or zig_normal (ZIG_NORMAL)
- * with a choice of keying; ZIG_KEY_INDEX gives exactly their outputs.
- * Arguments, layout and returns as theirs, plus ZIG_E_INVAL for an unknown
- * dist or keying.  With ZIG_KEY_PACKED a launch whose first vector-aligned
- * counter (offset + the unaligned head) is not a multiple of 2 (FP64) or 4
- * (FP32) still gives the same outputs, computing one block per output.
+ * with a choice of keying and of table width; (ZIG_KEY_INDEX, 8) gives
+ * exactly their outputs.  index_bits 8 uses the paper's i_max = 256 tables;
+ * 10 uses i_max = 1024 (Appendix D item 1: a 10-bit layer index, bits 0-9
+ * of the first word, the normal's sign in bit 10, alias column bits 0-9 and
+ * threshold bits 10-63; U as above), whose fast path covers 1020/1024
+ * (exponential) and 1021/1024 (normal) of the draws.  Packed FP32 words hold
+ * only 8 index bits, so (ZIG_KEY_PACKED, 10, ZIG_F32) is rejected.
+ * Arguments, layout and returns as zig_exponential's, plus ZIG_E_INVAL for
+ * an unknown dist, keying or index_bits.  With ZIG_KEY_PACKED a launch whose
+ * first vector-aligned counter (offset + the unaligned head) is not a
+ * multiple of 2 (FP64) or 4 (FP32) still gives the same outputs, computing
+ * one block per output.
  */
-zig_status zig_generate(zig_dist dist, zig_keying keying, void* out, uint64_t n, uint64_t seed,
-                        uint64_t offset, zig_dtype dtype, void* stream);
+zig_status zig_generate(zig_dist dist, zig_keying keying, int index_bits, void* out, uint64_t n,
+                        uint64_t seed, uint64_t offset, zig_dtype dtype, void* stream);
 
 /*
  * Launch-shape autotuning.  The paper tunes its CPU code by hand and has

@@ -64,7 +64,7 @@ _export_tables = _sig("zig_export_tables", _int, [_int, ctypes.POINTER(zig_table
 _exponential = _sig("zig_exponential", _int, [_vp, _u64, _u64, _u64, _int, _vp])
 _normal = _sig("zig_normal", _int, [_vp, _u64, _u64, _u64, _int, _vp])
 _status_poll = _sig("zig_status_poll", _int, [_vp])
-_generate = _sig("zig_generate", _int, [_int, _int, _vp, _u64, _u64, _u64, _int, _vp])
+_generate = _sig("zig_generate", _int, [_int, _int, _int, _vp, _u64, _u64, _u64, _int, _vp])
 ZIG_KEY_INDEX, ZIG_KEY_PACKED = 0, 1
 _moments_ws = _sig("zig_moments_workspace_bytes", ctypes.c_size_t, [_int, _int])
 _moments = _sig("zig_moments", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp, _vp,
@@ -75,6 +75,30 @@ _batch = _sig("zig_batch", _int, [_vp, ctypes.c_uint32, _vp, _vp, ctypes.c_size_
 _moments_noalloc = _sig("zig_moments_noalloc", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp,
                                                       _vp])
 _set_limits = _sig("zig_set_fringe_limits", _int, [_int, _int])
+
+
+class zig_tables_ex(ctypes.Structure):
+    _fields_ = [
+        ("dist", ctypes.c_int32), ("L", ctypes.c_int32), ("imax", ctypes.c_int32),
+        ("index_bits", ctypes.c_int32),
+        ("X", ctypes.c_double * 1025), ("f", ctypes.c_double * 1025),
+        ("dX", ctypes.c_double * 1025), ("df", ctypes.c_double * 1025),
+        ("A", ctypes.c_double * 1025),
+        ("eps", ctypes.c_double), ("tau", ctypes.c_double), ("rinv", ctypes.c_double),
+        ("X32", ctypes.c_float * 1025), ("f32", ctypes.c_float * 1025),
+        ("dX32", ctypes.c_float * 1025), ("df32", ctypes.c_float * 1025),
+        ("rinv32", ctypes.c_float), ("reserved", ctypes.c_float),
+        ("T", ctypes.c_uint64 * 1024), ("alias", ctypes.c_uint16 * 1024),
+    ]
+
+
+_export_tables_ex = _sig("zig_export_tables_ex", _int, [_int, _int, ctypes.POINTER(zig_tables_ex)])
+
+
+def zig_export_tables_ex(dist: int, index_bits: int) -> zig_tables_ex:
+    t = zig_tables_ex()
+    _check(_export_tables_ex(int(dist), int(index_bits), ctypes.byref(t)), "zig_export_tables_ex")
+    return t
 
 
 class zig_tune_entry(ctypes.Structure):
@@ -160,12 +184,12 @@ def zig_normal(out, n=None, seed: int = 0, offset: int = 0, dtype=None, stream=N
 
 
 def zig_generate(dist: int, keying: int, out, n=None, seed: int = 0, offset: int = 0, dtype=None,
-                 stream=None) -> None:
+                 stream=None, index_bits: int = 8) -> None:
     """zig_exponential / zig_normal with a keying (ZIG_KEY_INDEX or
-    ZIG_KEY_PACKED)."""
+    ZIG_KEY_PACKED) and a table width (index_bits 8 or 10)."""
     ptr, n, code = _out_args(out, n, dtype)
-    _check(_generate(int(dist), int(keying), ptr, n, seed & (2**64 - 1), offset & (2**64 - 1),
-                     code, _stream_handle(stream, out)), "zig_generate")
+    _check(_generate(int(dist), int(keying), int(index_bits), ptr, n, seed & (2**64 - 1),
+                     offset & (2**64 - 1), code, _stream_handle(stream, out)), "zig_generate")
 
 
 def zig_moments_workspace_bytes(dist: int, dtype: int) -> int:

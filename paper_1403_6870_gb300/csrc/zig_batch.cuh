@@ -258,7 +258,7 @@ __device__ ZIG_BATCH_RUN_ATTR void batch_run(BatchCtaState& sh, const BatchReq* 
   sink.b = sizeof(T) == 8 ? (T)q.b64 : (T)q.b32;
   const uint64_t seed = q.seed, tile0 = q.tile0;
   const RoundKeys rk = device_keys(seed);
-  gen_tiles<DIST, T, GenShape<T>, 0>(sh, sink, batch_sx<T>(sh, DIST), q.n, q.head, q.nvec, seed,
+  gen_tiles<DIST, T, GenShape<T>, 0, 8>(sh, sink, batch_sx<T>(sh, DIST), q.n, q.head, q.nvec, seed,
                                      q.offset, rk, lim, t0 - tile0, t1 - tile0, 1, t0 == tile0);
 }
 

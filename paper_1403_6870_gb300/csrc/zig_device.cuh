@@ -8,7 +8,9 @@
 //   5-8. rejection-sample overhang box j.
 // Words: from the 64-bit word w, i = bits 0-7, the normal's sign = bit 8,
 // U = bits 12-63 as m 2^-52 (FP32: bits 41-63 as m 2^-23); an alias word
-// gives column c = bits 0-7 and threshold t = bits 8-63.
+// gives column c = bits 0-7 and threshold t = bits 8-63.  With a 10-bit
+// index (i_max = 1024): i = bits 0-9, sign = bit 10, column = bits 0-9,
+// threshold = bits 10-63.
 #ifndef ZIG_DEVICE_CUH
 #define ZIG_DEVICE_CUH
 
@@ -22,19 +24,24 @@
 namespace zig {
 
 // ---------------------------------------------------------------------------
-// Device tables (one set per distribution; index = zig_dist)
+// Device tables (one set per distribution; index = zig_dist) for an index of
+// IB bits: i_max = 2^IB slots (8: the paper's 256; 10: the 1024 of
+// Appendix D item 1)
 // ---------------------------------------------------------------------------
-struct DevTab {
-  double X[256];   // X_i; entries beyond L_max are zero (never returned)
-  double f[257];   // heights f_0..f_L (normal: unnormalised)
-  double dX[257];  // X_{j-1} - X_j
-  double df[257];  // f_j - f_{j-1}
-  float X32[256];
-  float f32[257];
-  float dX32[257];
-  float df32[257];
-  unsigned long long T[256];  // alias thresholds (56-bit scale)
-  unsigned char alias[256];
+template <int IB>
+struct DevTabT {
+  static constexpr int kIMax = 1 << IB;
+  static constexpr int kBits = IB;
+  double X[kIMax];       // X_i; entries beyond L_max are zero (never returned)
+  double f[kIMax + 1];   // heights f_0..f_L (normal: unnormalised)
+  double dX[kIMax + 1];  // X_{j-1} - X_j
+  double df[kIMax + 1];  // f_j - f_{j-1}
+  float X32[kIMax];
+  float f32[kIMax + 1];
+  float dX32[kIMax + 1];
+  float df32[kIMax + 1];
+  unsigned long long T[kIMax];  // alias thresholds (scale 2^(64 - IB))
+  typename std::conditional<(IB <= 8), unsigned char, unsigned short>::type alias[kIMax];
   double tau;                  // exponential always-accept bound on ux + uy
   unsigned long long thr52;    // smallest integer >= tau 2^52
   unsigned int thr23;          // smallest integer >= tau 2^23
@@ -42,11 +49,24 @@ struct DevTab {
   float rinv32;
   int L;
 };
+typedef DevTabT<8> DevTab;
 
 // This header is included by exactly one translation unit (zig_gen.cu),
 // which owns the tables and the status word of each device.
 __device__ DevTab g_tab[2];
+__device__ DevTabT<10> g_tab10[2];
 __device__ unsigned int g_status;
+
+template <int IB>
+__device__ __forceinline__ const DevTabT<IB>& dev_tab(int dist);
+template <>
+__device__ __forceinline__ const DevTabT<8>& dev_tab<8>(int dist) {
+  return g_tab[dist];
+}
+template <>
+__device__ __forceinline__ const DevTabT<10>& dev_tab<10>(int dist) {
+  return g_tab10[dist];
+}
 
 constexpr unsigned kLoopLimitBit = 1u << ZIG_E_LOOP_LIMIT;
 
@@ -247,12 +267,18 @@ struct Prec<double> {
   }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  static __device__ __forceinline__ double X(const DevTab& t, int i) { return t.X[i]; }
-  static __device__ __forceinline__ double f(const DevTab& t, int i) { return t.f[i]; }
-  static __device__ __forceinline__ double dX(const DevTab& t, int i) { return t.dX[i]; }
-  static __device__ __forceinline__ double df(const DevTab& t, int i) { return t.df[i]; }
-  static __device__ __forceinline__ double rinv(const DevTab& t) { return t.rinv; }
-  static __device__ __forceinline__ UInt thr(const DevTab& t) { return t.thr52; }
+  template <class Tab>
+  static __device__ __forceinline__ double X(const Tab& t, int i) { return t.X[i]; }
+  template <class Tab>
+  static __device__ __forceinline__ double f(const Tab& t, int i) { return t.f[i]; }
+  template <class Tab>
+  static __device__ __forceinline__ double dX(const Tab& t, int i) { return t.dX[i]; }
+  template <class Tab>
+  static __device__ __forceinline__ double df(const Tab& t, int i) { return t.df[i]; }
+  template <class Tab>
+  static __device__ __forceinline__ double rinv(const Tab& t) { return t.rinv; }
+  template <class Tab>
+  static __device__ __forceinline__ UInt thr(const Tab& t) { return t.thr52; }
   static __device__ __forceinline__ double nan() {
     return __longlong_as_double(0x7FF8000000000000ll);
   }
@@ -273,19 +299,26 @@ struct Prec<float> {
   }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float X(const DevTab& t, int i) { return t.X32[i]; }
-  static __device__ __forceinline__ float f(const DevTab& t, int i) { return t.f32[i]; }
-  static __device__ __forceinline__ float dX(const DevTab& t, int i) { return t.dX32[i]; }
-  static __device__ __forceinline__ float df(const DevTab& t, int i) { return t.df32[i]; }
-  static __device__ __forceinline__ float rinv(const DevTab& t) { return t.rinv32; }
-  static __device__ __forceinline__ UInt thr(const DevTab& t) { return t.thr23; }
+  template <class Tab>
+  static __device__ __forceinline__ float X(const Tab& t, int i) { return t.X32[i]; }
+  template <class Tab>
+  static __device__ __forceinline__ float f(const Tab& t, int i) { return t.f32[i]; }
+  template <class Tab>
+  static __device__ __forceinline__ float dX(const Tab& t, int i) { return t.dX32[i]; }
+  template <class Tab>
+  static __device__ __forceinline__ float df(const Tab& t, int i) { return t.df32[i]; }
+  template <class Tab>
+  static __device__ __forceinline__ float rinv(const Tab& t) { return t.rinv32; }
+  template <class Tab>
+  static __device__ __forceinline__ UInt thr(const Tab& t) { return t.thr23; }
   static __device__ __forceinline__ float nan() { return __int_as_float(0x7FC00000); }
 };
 
 // Step 3: j from the alias table.
-__device__ __forceinline__ int alias_pick(const DevTab& t, uint64_t w) {
-  const int c = (int)(w & 0xFFu);
-  return (w >> 8) < t.T[c] ? c : (int)t.alias[c];
+template <class Tab>
+__device__ __forceinline__ int alias_pick(const Tab& t, uint64_t w) {
+  const int c = (int)(w & (uint64_t)(Tab::kIMax - 1));
+  return (w >> Tab::kBits) < t.T[c] ? c : (int)t.alias[c];
 }
 
 // FP32 approximation of U from its integer (top 24 bits at most).
@@ -312,8 +345,8 @@ constexpr float kPreTestMargin = 1.0f / 16384.0f;
 // 5); below the chord by more than eps they are accepted without a test
 // (Sec. 2, three regions); the rest get the exact test y < e^-x.  Normal:
 // the exact test y < e^{-x^2/2}.  On accept x = X_j + ux (X_{j-1} - X_j).
-template <int DIST, typename T>
-__device__ __forceinline__ bool overhang_attempt(const DevTab& t, int j,
+template <int DIST, typename T, class Tab>
+__device__ __forceinline__ bool overhang_attempt(const Tab& t, int j,
                                                  typename Prec<T>::UInt mx,
                                                  typename Prec<T>::UInt my, T& x) {
   typedef Prec<T> P;
@@ -355,14 +388,14 @@ __device__ __forceinline__ bool overhang_attempt(const DevTab& t, int j,
 // innermost first, so depth d adds X_0 d times after the final draw.
 // Steps 5-8 keep j on rejection and draw fresh (ux, uy); the first attempt
 // reuses U_1 as ux (its bits are disjoint from i).
-template <typename T, typename W>
-__device__ T exp_general(W& w, const DevTab& t, Limits lim, bool& err) {
+template <typename T, typename W, class Tab>
+__device__ T exp_general(W& w, const Tab& t, Limits lim, bool& err) {
   typedef Prec<T> P;
   int depth = 0;
   T x;
   for (;;) {
     const uint64_t w0 = w.next();
-    const int i = (int)(w0 & 0xFFu);
+    const int i = (int)(w0 & (uint64_t)(Tab::kIMax - 1));
     const typename P::UInt m1 = P::ubits(w0);
     if (i < t.L) {
       x = P::mul(P::val(m1), P::X(t, i));
@@ -379,7 +412,7 @@ __device__ T exp_general(W& w, const DevTab& t, Limits lim, bool& err) {
     typename P::UInt mx = m1;
     for (int att = 1;; ++att) {
       const typename P::UInt my = P::ubits(w.next());
-      if (overhang_attempt<ZIG_EXP, T>(t, j, mx, my, x)) break;
+      if (overhang_attempt<ZIG_EXP, T, Tab>(t, j, mx, my, x)) break;
       if (att >= lim.max_att) {
         err = true;
         return P::nan();
@@ -396,13 +429,12 @@ __device__ T exp_general(W& w, const DevTab& t, Limits lim, bool& err) {
 // beyond X_0 by Marsaglia-Tsang from two exponential draws (a = E_1 / X_0,
 // accept when 2 E_2 > a^2, return X_0 + a); overhangs by rejection against
 // e^{-x^2/2}, keeping j and redrawing both uniforms.
-template <typename T, typename W>
-__device__ T normal_general(W& w, const DevTab& te, const DevTab& tn, Limits lim,
-                            bool& err) {
+template <typename T, typename W, class Tab>
+__device__ T normal_general(W& w, const Tab& te, const Tab& tn, Limits lim, bool& err) {
   typedef Prec<T> P;
   const uint64_t w0 = w.next();
-  const int i = (int)(w0 & 0xFFu);
-  const bool negative = ((w0 >> 8) & 1u) != 0;
+  const int i = (int)(w0 & (uint64_t)(Tab::kIMax - 1));
+  const bool negative = ((w0 >> Tab::kBits) & 1u) != 0;
   const typename P::UInt m1 = P::ubits(w0);
   T x;
   if (i < tn.L) {
@@ -427,7 +459,7 @@ __device__ T normal_general(W& w, const DevTab& te, const DevTab& tn, Limits lim
       typename P::UInt mx = m1;
       for (int att = 1;; ++att) {
         const typename P::UInt my = P::ubits(w.next());
-        if (overhang_attempt<ZIG_NORMAL, T>(tn, j, mx, my, x)) break;
+        if (overhang_attempt<ZIG_NORMAL, T, Tab>(tn, j, mx, my, x)) break;
         if (att >= lim.max_att) {
           err = true;
           return P::nan();
@@ -440,14 +472,14 @@ __device__ T normal_general(W& w, const DevTab& te, const DevTab& tn, Limits lim
 }
 
 // The complete sampler for counter g of key seed; KEY 0: per-index words,
-// KEY 1: packed keying.
-template <int DIST, typename T, int KEY = 0>
+// KEY 1: packed keying; IB: index bits of the tables.
+template <int DIST, typename T, int KEY = 0, int IB = 8>
 __device__ __noinline__ T sample_general(uint64_t seed, uint64_t g, Limits lim) {
   typename std::conditional<KEY == 0, Words, PackedWords<T>>::type w(seed, g);
   bool err = false;
   T x = (DIST == ZIG_EXP)
-            ? exp_general<T>(w, g_tab[ZIG_EXP], lim, err)
-            : normal_general<T>(w, g_tab[ZIG_EXP], g_tab[ZIG_NORMAL], lim, err);
+            ? exp_general<T>(w, dev_tab<IB>(ZIG_EXP), lim, err)
+            : normal_general<T>(w, dev_tab<IB>(ZIG_EXP), dev_tab<IB>(ZIG_NORMAL), lim, err);
   if (err) atomicOr(&g_status, kLoopLimitBit);
   return x;
 }
@@ -458,22 +490,23 @@ __device__ __noinline__ T sample_general(uint64_t seed, uint64_t g, Limits lim) 
 // x = RN(U X_i) computed as fma(1 + U, X_i, -X_i): (1 + U) X_i - X_i equals
 // U X_i exactly and the FMA rounds once.  The normal's sign (bit 8) is put
 // on the result's sign bit.
-template <int DIST>
+template <int DIST, int IB = 8>
 __device__ __forceinline__ double fast_value(uint32_t lo, uint32_t hi, const double* sX) {
-  const double X = sX[lo & 0xFFu];
+  const double X = sX[lo & ((1u << IB) - 1u)];
   const double one_u = __hiloint2double((int)(0x3FF00000u | (hi >> 12)),
                                         (int)__funnelshift_r(lo, hi, 12));
   const double x = __fma_rn(one_u, X, -X);
   if (DIST == ZIG_EXP) return x;
-  return __hiloint2double(__double2hiint(x) ^ (int)((lo & 0x100u) << 23), __double2loint(x));
+  return __hiloint2double(__double2hiint(x) ^ (int)((lo & (1u << IB)) << (31 - IB)),
+                          __double2loint(x));
 }
 
-template <int DIST>
+template <int DIST, int IB = 8>
 __device__ __forceinline__ float fast_value(uint32_t lo, uint32_t hi, const float* sX) {
-  const float X = sX[lo & 0xFFu];
+  const float X = sX[lo & ((1u << IB) - 1u)];
   const float x = __fmaf_rn(__int_as_float((int)(0x3F800000u | (hi >> 9))), X, -X);
   if (DIST == ZIG_EXP) return x;
-  return __int_as_float(__float_as_int(x) ^ (int)((lo & 0x100u) << 23));
+  return __int_as_float(__float_as_int(x) ^ (int)((lo & (1u << IB)) << (31 - IB)));
 }
 
 }  // namespace zig

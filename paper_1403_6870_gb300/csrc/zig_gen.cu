@@ -195,10 +195,10 @@ struct WarpQueues {
   int nq, nr, nt;
 };
 
-// Shared state of one CTA.
-template <typename T>
+// Shared state of one CTA (X_i of an index of IB bits).
+template <typename T, int IB = 8>
 struct CtaState {
-  T sX[256];
+  T sX[1 << IB];
   WarpQueues wq[kWarps];
 };
 
@@ -287,6 +287,13 @@ __device__ __forceinline__ void put_signed(Sink& sink, uint64_t p, T x, bool neg
   sink.put(p, (DIST == ZIG_NORMAL && negative) ? -x : x);
 }
 
+// A retry's state word: overhang j in bits 0-10 (j < 1024 at either index
+// width), the normal's sign in bit 11, completed attempts in bits 12-31
+// (below the 2^20 cap of zig_set_fringe_limits), the next block in 32-63.
+constexpr uint64_t kStateJMask = 0x7FFull;
+constexpr int kStateSignBit = 11;
+constexpr int kStateAttShift = 12;
+
 // Fringe queue lengths (warp-uniform): retries and tails.
 struct SideCounts {
   int retry, tail;
@@ -312,12 +319,12 @@ __device__ __forceinline__ int claim(bool f, int& n) {
 // KEY 0 (per-index words): block 0 gives U_1 (as ux) and the alias word,
 // block 1's first word uy.  KEY 1 (packed keying): U_1 from the packed
 // first word, the alias word and uy from private block 0.
-template <int DIST, typename T, uint64_t kPosMask, int KEY, typename Sink, typename State>
+template <int DIST, typename T, uint64_t kPosMask, int KEY, int IB, typename Sink, typename State>
 __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const RoundKeys& rk,
                                           Limits lim, bool active, uint64_t item, State& sh,
                                           SideCounts& c) {
   typedef Prec<T> P;
-  const DevTab& t = g_tab[DIST];
+  const DevTabT<IB>& t = dev_tab<IB>(DIST);
   const bool whole = (item & kWholeTag) != 0;
   const uint64_t p = item & ~kWholeTag;  // the queued value
   const uint64_t g = offset + (p & kPosMask);
@@ -333,7 +340,7 @@ __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const Rou
     aw = pack(b1.x, b1.y);
   }
   const int j = alias_pick(t, aw);
-  const bool negative = ((w0 >> 8) & 1u) != 0;
+  const bool negative = ((w0 >> IB) & 1u) != 0;
   const bool overhang = active && !whole && j != 0;
   bool retry = false;
   uint64_t state = 0, next = 0;
@@ -350,7 +357,7 @@ __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const Rou
       retry = true;
       // next block: per-index 2 (block 1's second word saved as the next
       // ux); packed: private block 1
-      state = (uint64_t)j | ((uint64_t)negative << 8) | (1ull << 9) |
+      state = (uint64_t)j | ((uint64_t)negative << kStateSignBit) | (1ull << kStateAttShift) |
               ((KEY == 0 ? 2ull : 1ull) << 32);
       next = KEY == 0 ? pack(b1.z, b1.w) : 0ull;
     }
@@ -368,19 +375,18 @@ __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const Rou
 
 // Stage 2 (one retry per lane): ux is the saved word, uy the first word of
 // the next block, whose second word is saved for the following attempt.  j
-// is kept (Table 1 step 8 returns to step 4).  State: j in bits 0-7, the
-// normal's sign in bit 8, completed attempts in bits 9-31, next block in
-// bits 32-63.
-template <int DIST, typename T, uint64_t kPosMask, int KEY, typename Sink, typename State>
+// is kept (Table 1 step 8 returns to step 4).  State as laid out above
+// (kStateJMask, kStateSignBit, kStateAttShift).
+template <int DIST, typename T, uint64_t kPosMask, int KEY, int IB, typename Sink, typename State>
 __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const RoundKeys& rk,
                                             Limits lim, bool active, uint64_t p,
                                             uint64_t state, uint64_t word, State& sh,
                                             SideCounts& c) {
   typedef Prec<T> P;
-  const DevTab& t = g_tab[DIST];
-  const int j = (int)(state & 0xFFu);
-  const bool negative = ((state >> 8) & 1u) != 0;
-  const uint32_t att = (uint32_t)(state >> 9) & 0x7FFFFFu;
+  const DevTabT<IB>& t = dev_tab<IB>(DIST);
+  const int j = (int)(state & kStateJMask);
+  const bool negative = ((state >> kStateSignBit) & 1u) != 0;
+  const uint32_t att = (uint32_t)(state >> kStateAttShift) & 0xFFFFFu;
   const uint32_t blk = (uint32_t)(state >> 32);
   bool retry = false;
   uint64_t nstate = 0, next = 0;
@@ -398,7 +404,8 @@ __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const R
       atomicOr(&g_status, kLoopLimitBit);
     } else {
       retry = true;
-      nstate = (state & 0x1FFull) | ((uint64_t)(att + 1) << 9) | ((uint64_t)(blk + 1) << 32);
+      nstate = (state & ((1ull << kStateAttShift) - 1ull)) |
+               ((uint64_t)(att + 1) << kStateAttShift) | ((uint64_t)(blk + 1) << 32);
       next = KEY == 0 ? pack(b.z, b.w) : 0ull;
     }
   }
@@ -413,7 +420,7 @@ __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const R
 // Run the retry and tail stages while they hold `need` or more
 // entries (at most 32 per batch).  Each side queue holds fewer than 32
 // entries before a stage-1 batch, so it stays within its 64 slots.
-template <int DIST, typename T, int KEY, typename Sink, typename State>
+template <int DIST, typename T, int KEY, int IB, typename Sink, typename State>
 __device__ __forceinline__ void side_stages(Sink& sink, uint64_t seed, uint64_t offset,
                                             const RoundKeys& rk, Limits lim, int need,
                                             State& sh, SideCounts& c) {
@@ -428,14 +435,14 @@ __device__ __forceinline__ void side_stages(Sink& sink, uint64_t seed, uint64_t 
                      w = active ? sh.rw[k] : 0;
       c.retry -= take;
       __syncwarp();  // slots read before they are refilled
-      stage_retry<DIST, T, kPos, KEY>(sink, offset, rk, lim, active, p, st, w, sh, c);
+      stage_retry<DIST, T, kPos, KEY, IB>(sink, offset, rk, lim, active, p, st, w, sh, c);
     } else if (c.tail >= need) {
       const int take = c.tail < 32 ? c.tail : 32;
       const bool active = lane < take;
       const uint64_t p = active ? sh.tq[c.tail - take + lane] : 0;
       c.tail -= take;
       __syncwarp();
-      if (active) sink.put(p, sample_general<DIST, T, KEY>(seed, offset + p, lim));
+      if (active) sink.put(p, sample_general<DIST, T, KEY, IB>(seed, offset + p, lim));
     } else {
       break;
     }
@@ -468,7 +475,7 @@ constexpr int kPackedUnrollR = ZIG_PACKED_UNROLL_R;
 // NOWRAP: the low counter words do not wrap inside the run.  full: every
 // vector lies inside the output (else vector r exists only if
 // v0 + r kPThreads < nvec).
-template <int DIST, typename T, typename Shp, bool NOWRAP, typename Sink>
+template <int DIST, typename T, typename Shp, bool NOWRAP, int IB, typename Sink>
 __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
     Sink& sink, uint64_t g0, uint64_t v0, uint64_t nvec, bool full, const RoundKeys& rk,
     const T* sX, uint32_t L) {
@@ -484,8 +491,8 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
     for (int k = 0; k < V; ++k) {
       const uint32_t d = (uint32_t)(r * kPThreads * V + k);
       const uint2 w = NOWRAP ? run.word(d, rk) : philox_first(g0 + d, rk);
-      v[k] = fast_value<DIST>(w.x, w.y, sX);
-      f |= (unsigned)((w.x & 0xFFu) >= L) << k;
+      v[k] = fast_value<DIST, IB>(w.x, w.y, sX);
+      f |= (unsigned)((w.x & ((1u << IB) - 1u)) >= L) << k;
     }
     const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
     if (full || vi < nvec) {
@@ -502,7 +509,7 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
 // vector takes V / P blocks.  MODE 0: the vector's counters start at a
 // multiple of P and the run's block counters do not wrap their low word;
 // MODE 1: aligned, with wrap; MODE 2: not aligned (one block per output).
-template <int DIST, typename T, typename Shp, int MODE, typename Sink>
+template <int DIST, typename T, typename Shp, int MODE, int IB, typename Sink>
 __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
     Sink& sink, uint64_t g0, uint64_t v0, uint64_t nvec, bool full, const RoundKeys& rk,
     const T* sX, uint32_t L) {
@@ -510,6 +517,8 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
   constexpr int P = sizeof(T) == 8 ? 2 : 4, SH = sizeof(T) == 8 ? 1 : 2, B = V / P;
   static_assert(V % P == 0, "a vector holds whole blocks");
   static_assert(V * R <= 64, "at most 64 outputs per thread and tile");
+  static_assert(IB == 8 || sizeof(T) == 8, "a 32-bit packed word has room for 8 index bits");
+  constexpr uint32_t kIM = (1u << IB) - 1u;
   FringeMask<V * R> fm = 0;
   const uint64_t h0 = g0 >> SH;
   const RunState run(h0, rk);
@@ -523,16 +532,16 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
         const uint32_t d = (uint32_t)(r * kPThreads * B + b);
         const uint4 w = MODE == 0 ? run.block(d, rk) : philox_block(h0 + d, 0u, rk);
         if (sizeof(T) == 8) {
-          v[2 * b] = fast_value<DIST>(w.x, w.y, sX);
-          v[2 * b + 1] = fast_value<DIST>(w.z, w.w, sX);
-          f |= ((unsigned)((w.x & 0xFFu) >= L) | ((unsigned)((w.z & 0xFFu) >= L) << 1)) << (2 * b);
+          v[2 * b] = fast_value<DIST, IB>(w.x, w.y, sX);
+          v[2 * b + 1] = fast_value<DIST, IB>(w.z, w.w, sX);
+          f |= ((unsigned)((w.x & kIM) >= L) | ((unsigned)((w.z & kIM) >= L) << 1)) << (2 * b);
         } else {
-          v[4 * b] = fast_value<DIST>(w.x, w.x, sX);
-          v[4 * b + 1] = fast_value<DIST>(w.y, w.y, sX);
-          v[4 * b + 2] = fast_value<DIST>(w.z, w.z, sX);
-          v[4 * b + 3] = fast_value<DIST>(w.w, w.w, sX);
-          f |= ((unsigned)((w.x & 0xFFu) >= L) | ((unsigned)((w.y & 0xFFu) >= L) << 1) |
-                ((unsigned)((w.z & 0xFFu) >= L) << 2) | ((unsigned)((w.w & 0xFFu) >= L) << 3))
+          v[4 * b] = fast_value<DIST, IB>(w.x, w.x, sX);
+          v[4 * b + 1] = fast_value<DIST, IB>(w.y, w.y, sX);
+          v[4 * b + 2] = fast_value<DIST, IB>(w.z, w.z, sX);
+          v[4 * b + 3] = fast_value<DIST, IB>(w.w, w.w, sX);
+          f |= ((unsigned)((w.x & kIM) >= L) | ((unsigned)((w.y & kIM) >= L) << 1) |
+                ((unsigned)((w.z & kIM) >= L) << 2) | ((unsigned)((w.w & kIM) >= L) << 3))
                << (4 * b);
         }
       }
@@ -541,8 +550,8 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
       for (int k = 0; k < V; ++k) {
         const uint64_t g = g0 + (uint64_t)(r * kPThreads * V + k);
         const uint64_t w = packed_word_of<T>(philox_block(g >> SH, 0u, rk), g);
-        v[k] = fast_value<DIST>((uint32_t)w, (uint32_t)(w >> 32), sX);
-        f |= (unsigned)(((uint32_t)w & 0xFFu) >= L) << k;
+        v[k] = fast_value<DIST, IB>((uint32_t)w, (uint32_t)(w >> 32), sX);
+        f |= (unsigned)(((uint32_t)w & kIM) >= L) << k;
       }
     }
     const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
@@ -579,7 +588,7 @@ struct ReduceOut {
 #ifndef ZIG_FRINGE_ATTR
 #define ZIG_FRINGE_ATTR __forceinline__
 #endif
-template <int DIST, typename T, int KEY, typename Sink>
+template <int DIST, typename T, int KEY, int IB, typename Sink>
 __device__ ZIG_FRINGE_ATTR Sink fringe_work(Sink sink, WarpQueues& wq, uint64_t seed,
                                             uint64_t offset, Limits lim, bool drain) {
   const int lane = threadIdx.x & 31;
@@ -593,11 +602,11 @@ __device__ ZIG_FRINGE_ATTR Sink fringe_work(Sink sink, WarpQueues& wq, uint64_t 
     const uint64_t item = active ? wq.q[nq - take + lane] : 0;
     nq -= take;
     __syncwarp();
-    stage_new<DIST, T, ~kWholeTag, KEY>(sink, offset, rk, lim, active, item, wq, c);
+    stage_new<DIST, T, ~kWholeTag, KEY, IB>(sink, offset, rk, lim, active, item, wq, c);
     __syncwarp();
-    side_stages<DIST, T, KEY>(sink, seed, offset, rk, lim, 32, wq, c);
+    side_stages<DIST, T, KEY, IB>(sink, seed, offset, rk, lim, 32, wq, c);
   }
-  if (drain) side_stages<DIST, T, KEY>(sink, seed, offset, rk, lim, 1, wq, c);
+  if (drain) side_stages<DIST, T, KEY, IB>(sink, seed, offset, rk, lim, 1, wq, c);
   __syncwarp();
   if (lane == 0) {
     wq.nq = nq;
@@ -618,7 +627,7 @@ __device__ ZIG_FRINGE_ATTR Sink fringe_work(Sink sink, WarpQueues& wq, uint64_t 
 // index is not below L_max, runs the fringe stages for every 32 of them and
 // drains its queues before returning; on return every output of the CTA's
 // tiles has its final value (the warps have not synchronised).
-template <int DIST, typename T, typename Shp, int KEY, typename Sink, typename State>
+template <int DIST, typename T, typename Shp, int KEY, int IB, typename Sink, typename State>
 __device__ __forceinline__ void gen_tiles(State& sh, Sink& sink, const T* sX, uint64_t n,
                                           uint64_t head, uint64_t nvec, uint64_t seed,
                                           uint64_t offset, const RoundKeys& rk, Limits lim,
@@ -629,7 +638,7 @@ __device__ __forceinline__ void gen_tiles(State& sh, Sink& sink, const T* sX, ui
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   WarpQueues& wq = sh.wq[tid >> 5];
-  const uint32_t L = (uint32_t)g_tab[DIST].L;
+  const uint32_t L = (uint32_t)dev_tab<IB>(DIST).L;
   const uint64_t body_end = head + nvec * V;
   {
     // head and tail elements (fewer than V each) take the whole sampler
@@ -660,20 +669,20 @@ __device__ __forceinline__ void gen_tiles(State& sh, Sink& sink, const T* sX, ui
     const uint64_t g0 = offset + p0;
     const bool full = (tile + 1) * kTile <= nvec;
     FringeMask<V * R> fm;  // outputs of this thread whose layer index is >= L_max
-    if (KEY == 0) {
+    if constexpr (KEY == 0) {
       if ((uint32_t)g0 <= 0xFFFFFFFFu - kSpan)
-        fm = producer_tile<DIST, T, Shp, true>(sink, g0, v0, nvec, full, rk, sX, L);
+        fm = producer_tile<DIST, T, Shp, true, IB>(sink, g0, v0, nvec, full, rk, sX, L);
       else
-        fm = producer_tile<DIST, T, Shp, false>(sink, g0, v0, nvec, full, rk, sX, L);
+        fm = producer_tile<DIST, T, Shp, false, IB>(sink, g0, v0, nvec, full, rk, sX, L);
     } else {
       constexpr int P = sizeof(T) == 8 ? 2 : 4, SH = sizeof(T) == 8 ? 1 : 2;
       constexpr uint32_t kSpanB = (uint32_t)((R - 1) * kPThreads * (V / P) + (V / P - 1));
       if (g0 % P != 0)
-        fm = producer_tile_packed<DIST, T, Shp, 2>(sink, g0, v0, nvec, full, rk, sX, L);
+        fm = producer_tile_packed<DIST, T, Shp, 2, IB>(sink, g0, v0, nvec, full, rk, sX, L);
       else if ((uint32_t)(g0 >> SH) <= 0xFFFFFFFFu - kSpanB)
-        fm = producer_tile_packed<DIST, T, Shp, 0>(sink, g0, v0, nvec, full, rk, sX, L);
+        fm = producer_tile_packed<DIST, T, Shp, 0, IB>(sink, g0, v0, nvec, full, rk, sX, L);
       else
-        fm = producer_tile_packed<DIST, T, Shp, 1>(sink, g0, v0, nvec, full, rk, sX, L);
+        fm = producer_tile_packed<DIST, T, Shp, 1, IB>(sink, g0, v0, nvec, full, rk, sX, L);
     }
     // queue the positions; run the fringe stages whenever 32 are queued
     FringeMask<V * R> m = fm;
@@ -697,32 +706,33 @@ __device__ __forceinline__ void gen_tiles(State& sh, Sink& sink, const T* sX, ui
       const int added = total < kQueue - nq ? total : kQueue - nq;
       if (lane == 0) wq.nq = nq + added;
       __syncwarp();
-      if (nq + added >= 32) sink = fringe_work<DIST, T, KEY>(sink, wq, seed, offset, lim, false);
+      if (nq + added >= 32)
+        sink = fringe_work<DIST, T, KEY, IB>(sink, wq, seed, offset, lim, false);
     }
   }
-  sink = fringe_work<DIST, T, KEY>(sink, wq, seed, offset, lim, true);
+  sink = fringe_work<DIST, T, KEY, IB>(sink, wq, seed, offset, lim, true);
 }
 
 // One launch covers outputs [0, n) (layout as in gen_tiles); CTA b takes
 // tiles b, b + gridDim.x, ... and CTA 0 the head and tail elements.
-template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>, int KEY = 0>
+template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>, int KEY = 0, int IB = 8>
 __global__ void __launch_bounds__(kThreads, Shp::MB)
     gen_kernel(Sink sink, uint64_t n, uint32_t head, uint64_t nvec, uint64_t seed,
                uint64_t offset, const RoundKeys rk, Limits lim, ReduceOut red) {
   constexpr int R = Shp::R;
   constexpr int kTile = kPThreads * R;
-  __shared__ CtaState<T> sh;
+  __shared__ CtaState<T, IB> sh;
   __shared__ unsigned shist[Sink::kReduce ? kBins : 1];
 
   const int tid = threadIdx.x;
-  for (int k = tid; k < 256; k += kThreads) sh.sX[k] = Prec<T>::X(g_tab[DIST], k);
+  for (int k = tid; k < (1 << IB); k += kThreads) sh.sX[k] = Prec<T>::X(dev_tab<IB>(DIST), k);
   if (Sink::kReduce)
     for (int k = tid; k < kBins; k += kThreads) shist[k] = 0u;
   if constexpr (Sink::kReduce) sink.init(shist);
   __syncthreads();
 
   const uint64_t ntiles = (nvec + kTile - 1) / kTile;
-  gen_tiles<DIST, T, Shp, KEY>(sh, sink, sh.sX, n, head, nvec, seed, offset, rk, lim,
+  gen_tiles<DIST, T, Shp, KEY, IB>(sh, sink, sh.sX, n, head, nvec, seed, offset, rk, lim,
                                blockIdx.x, ntiles, gridDim.x, blockIdx.x == 0);
 
   if constexpr (Sink::kReduce) {
@@ -772,6 +782,8 @@ constexpr int kMaxDevices = 64;
 
 std::mutex g_mu;
 zig_tables_export g_host[2];
+zig_tables_ex g_host8ex[2];  // i_max = 256 in the wide layout
+zig_tables_ex g_host10[2];   // i_max = 1024
 std::atomic<bool> g_host_ready{false};
 std::atomic<int> g_max_att{64};
 std::atomic<int> g_max_tail{16};
@@ -799,13 +811,17 @@ zig_status ensure_host_tables() {
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_host_ready.load()) return ZIG_OK;
   if (build_host_tables(&g_host[0], &g_host[1]) != 0) return ZIG_E_TABLE;
+  if (build_host_tables_ex(8, &g_host8ex[0], &g_host8ex[1]) != 0) return ZIG_E_TABLE;
+  if (build_host_tables_ex(10, &g_host10[0], &g_host10[1]) != 0) return ZIG_E_TABLE;
   g_host_ready.store(true, std::memory_order_release);
   return ZIG_OK;
 }
 
-void to_device_layout(const zig_tables_export& h, DevTab* d) {
+template <class Host, int IB>
+void to_device_layout(const Host& h, DevTabT<IB>* d) {
+  constexpr int kIMax = 1 << IB;
   std::memset(d, 0, sizeof(*d));
-  for (int k = 0; k <= h.L && k < 256; ++k) {
+  for (int k = 0; k <= h.L && k < kIMax; ++k) {
     d->X[k] = h.X[k];
     d->X32[k] = h.X32[k];
   }
@@ -817,7 +833,7 @@ void to_device_layout(const zig_tables_export& h, DevTab* d) {
     d->dX32[k] = h.dX32[k];
     d->df32[k] = h.df32[k];
   }
-  for (int c = 0; c < 256; ++c) {
+  for (int c = 0; c < kIMax; ++c) {
     d->T[c] = h.T[c];
     d->alias[c] = h.alias[c];
   }
@@ -852,13 +868,13 @@ RoundKeys round_keys(uint64_t seed) {
   return rk;
 }
 
-template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>, int KEY = 0>
+template <int DIST, typename T, typename Sink, typename Shp = GenShape<T>, int KEY = 0, int IB = 8>
 int occupancy_blocks(int dev) {
   static std::atomic<int> cache[kMaxDevices];
   int v = cache[dev].load(std::memory_order_relaxed);
   if (v > 0) return v;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gen_kernel<DIST, T, Sink, Shp, KEY>,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gen_kernel<DIST, T, Sink, Shp, KEY, IB>,
                                                     kThreads, 0) != cudaSuccess ||
       occ < 1) {
     cudaGetLastError();
@@ -870,7 +886,7 @@ int occupancy_blocks(int dev) {
 
 // Materialising launch of shape Shp with at most bps CTAs per SM (0: as
 // many as fit).
-template <int DIST, typename T, typename Shp, int KEY = 0>
+template <int DIST, typename T, typename Shp, int KEY = 0, int IB = 8>
 zig_status launch_gen(void* out, uint64_t n, uint64_t seed, uint64_t offset,
                       cudaStream_t stream, int dev, int bps) {
   constexpr int V = Shp::V, R = Shp::R;
@@ -879,14 +895,14 @@ zig_status launch_gen(void* out, uint64_t n, uint64_t seed, uint64_t offset,
   const uint64_t head = align_elems < n ? align_elems : n;
   const uint64_t nvec = (n - head) / V;
   const uint64_t tiles = (nvec + (uint64_t)kPThreads * R - 1) / ((uint64_t)kPThreads * R);
-  int occ = occupancy_blocks<DIST, T, StoreSink<T>, Shp, KEY>(dev);
+  int occ = occupancy_blocks<DIST, T, StoreSink<T>, Shp, KEY, IB>(dev);
   if (bps > 0 && bps < occ) occ = bps;
   const uint64_t cap = (uint64_t)g_dev[dev].sms * (uint64_t)occ;
   uint64_t grid = tiles < cap ? tiles : cap;
   if (grid < 1) grid = 1;
   Limits lim{g_max_att.load(), g_max_tail.load()};
   StoreSink<T> sink{(T*)out, head};
-  gen_kernel<DIST, T, StoreSink<T>, Shp, KEY><<<(unsigned)grid, kThreads, 0, stream>>>(
+  gen_kernel<DIST, T, StoreSink<T>, Shp, KEY, IB><<<(unsigned)grid, kThreads, 0, stream>>>(
       sink, n, (uint32_t)head, nvec, seed, offset, round_keys(seed), lim, ReduceOut{});
   if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
   return ZIG_OK;
@@ -1040,10 +1056,14 @@ void apply_cached(int dev) {
 }
 
 zig_status generate(int dist, void* out, uint64_t n, uint64_t seed, uint64_t offset,
-                    zig_dtype dtype, void* stream, int keying = ZIG_KEY_INDEX) {
+                    zig_dtype dtype, void* stream, int keying = ZIG_KEY_INDEX,
+                    int index_bits = 8) {
   if (dtype != ZIG_F32 && dtype != ZIG_F64) return ZIG_E_INVAL;
   if (dist != ZIG_EXP && dist != ZIG_NORMAL) return ZIG_E_INVAL;
   if (keying != ZIG_KEY_INDEX && keying != ZIG_KEY_PACKED) return ZIG_E_INVAL;
+  if (index_bits != 8 && index_bits != 10) return ZIG_E_INVAL;
+  // a packed FP32 word (32 bits) holds 8 index bits, a sign and 23 bits of U
+  if (index_bits == 10 && keying == ZIG_KEY_PACKED && dtype == ZIG_F32) return ZIG_E_INVAL;
   if (n == 0) return ZIG_OK;
   if (out == nullptr) return ZIG_E_INVAL;
   const size_t es = dtype == ZIG_F64 ? 8 : 4;
@@ -1055,6 +1075,22 @@ zig_status generate(int dist, void* out, uint64_t n, uint64_t seed, uint64_t off
   if (st != ZIG_OK) return st;
   if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
   cudaStream_t s = (cudaStream_t)stream;
+  if (index_bits == 10) {
+    if (keying == ZIG_KEY_PACKED)
+      return dist == ZIG_EXP ? launch_gen<ZIG_EXP, double, PackedShape<double>, 1, 10>(
+                                   out, n, seed, offset, s, dev, 0)
+                             : launch_gen<ZIG_NORMAL, double, PackedShape<double>, 1, 10>(
+                                   out, n, seed, offset, s, dev, 0);
+    if (dist == ZIG_EXP)
+      return dtype == ZIG_F64 ? launch_gen<ZIG_EXP, double, GenShape<double>, 0, 10>(
+                                    out, n, seed, offset, s, dev, 0)
+                              : launch_gen<ZIG_EXP, float, GenShape<float>, 0, 10>(
+                                    out, n, seed, offset, s, dev, 0);
+    return dtype == ZIG_F64 ? launch_gen<ZIG_NORMAL, double, GenShape<double>, 0, 10>(
+                                  out, n, seed, offset, s, dev, 0)
+                            : launch_gen<ZIG_NORMAL, float, GenShape<float>, 0, 10>(
+                                  out, n, seed, offset, s, dev, 0);
+  }
   if (keying == ZIG_KEY_PACKED) {
     if (dist == ZIG_EXP)
       return dtype == ZIG_F64 ? launch_gen<ZIG_EXP, double, PackedShape<double>, 1>(
@@ -1130,12 +1166,16 @@ zig_status zig_build_tables(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_dev[dev].ready.load()) return ZIG_OK;
   static DevTab h[2];
+  static DevTabT<10> h10[2];
   to_device_layout(g_host[0], &h[0]);
   to_device_layout(g_host[1], &h[1]);
+  to_device_layout(g_host10[0], &h10[0]);
+  to_device_layout(g_host10[1], &h10[1]);
   void* status = nullptr;
   void* scratch = nullptr;
   int sms = 0;
   if (cudaMemcpyToSymbol(g_tab, h, sizeof(h)) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_tab10, h10, sizeof(h10)) != cudaSuccess ||
       cudaGetSymbolAddress(&status, g_status) != cudaSuccess ||
       cudaGetSymbolAddress(&scratch, g_moment_scratch) != cudaSuccess ||
       cudaMemset(status, 0, sizeof(unsigned int)) != cudaSuccess ||
@@ -1276,6 +1316,16 @@ zig_status zig_export_tables(zig_dist dist, zig_tables_export* h_out) {
   return ZIG_OK;
 }
 
+zig_status zig_export_tables_ex(zig_dist dist, int index_bits, zig_tables_ex* h_out) {
+  if (h_out == nullptr || (dist != ZIG_EXP && dist != ZIG_NORMAL) ||
+      (index_bits != 8 && index_bits != 10))
+    return ZIG_E_INVAL;
+  zig_status st = ensure_host_tables();
+  if (st != ZIG_OK) return st;
+  *h_out = index_bits == 10 ? g_host10[dist] : g_host8ex[dist];
+  return ZIG_OK;
+}
+
 zig_status zig_exponential(void* out, uint64_t n, uint64_t seed, uint64_t offset,
                            zig_dtype dtype, void* stream) {
   return generate(ZIG_EXP, out, n, seed, offset, dtype, stream);
@@ -1286,9 +1336,9 @@ zig_status zig_normal(void* out, uint64_t n, uint64_t seed, uint64_t offset, zig
   return generate(ZIG_NORMAL, out, n, seed, offset, dtype, stream);
 }
 
-zig_status zig_generate(zig_dist dist, zig_keying keying, void* out, uint64_t n, uint64_t seed,
-                        uint64_t offset, zig_dtype dtype, void* stream) {
-  return generate(dist, out, n, seed, offset, dtype, stream, keying);
+zig_status zig_generate(zig_dist dist, zig_keying keying, int index_bits, void* out, uint64_t n,
+                        uint64_t seed, uint64_t offset, zig_dtype dtype, void* stream) {
+  return generate(dist, out, n, seed, offset, dtype, stream, keying, index_bits);
 }
 
 size_t zig_moments_workspace_bytes(zig_dist dist, zig_dtype dtype) {

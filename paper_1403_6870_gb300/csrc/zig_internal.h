@@ -12,6 +12,8 @@ namespace zig {
 // Host construction of both distributions' tables (zig_tables.cpp).
 // Returns 0 on success.
 int build_host_tables(zig_tables_export* exp_tab, zig_tables_export* nrm_tab);
+// The same at i_max = 2^ibits (ibits 8 or 10) in the wide layout.
+int build_host_tables_ex(int ibits, zig_tables_ex* exp_tab, zig_tables_ex* nrm_tab);
 
 // Host tables, built once per process (zig_gen.cu).
 const zig_tables_export* host_tables(int dist);

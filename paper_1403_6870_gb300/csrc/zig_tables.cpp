@@ -7,7 +7,8 @@
 // none fits (L_max of them); the overhangs A_j to the right of each layer,
 // the tail A_0 beyond X_0 and the cap above the last layer hold the rest of
 // the mass.  The tables are computed in binary128 and rounded to binary64
-// (Appendix B) and, for the FP32 generator, to binary32.
+// (Appendix B) and, for the FP32 generator, to binary32.  i_max is 256 (the
+// paper's tables) or 1024 (the variant of Appendix D item 1).
 //
 // Root finding here is a bracketed Newton iteration (Newton step when it
 // stays inside the bracket and shrinks it, bisection otherwise); both roots
@@ -89,22 +90,21 @@ double round_down(quad v) {
 }
 
 // Deterministic integer alias table (Walker/Vose; the paper cites Smith
-// 2002 for O(1) sampling of j ~ A).  Column capacity K = 2^56, 256
-// columns, weights summing to 256 K.  Worklists are FIFO queues filled in
-// increasing index order; the head of "small" is paired with the head of
-// "large"; a large entry whose remaining weight drops below K moves to the
-// back of "small".
-void vose(const std::vector<uint64_t>& q, uint64_t T[256], uint8_t alias[256]) {
-  const uint64_t K = (uint64_t)1 << 56;
+// 2002 for O(1) sampling of j ~ A).  cols = i_max columns of capacity
+// K = 2^64 / cols, weights summing to 2^64.  Worklists are FIFO queues
+// filled in increasing index order; the head of "small" is paired with the
+// head of "large"; a large entry whose remaining weight drops below K moves
+// to the back of "small".
+void vose(const std::vector<uint64_t>& q, int cols, uint64_t K, uint64_t* T, uint16_t* alias) {
   std::vector<uint64_t> rem(q);
   std::deque<int> small, large;
-  for (int j = 0; j < 256; ++j) (rem[j] < K ? small : large).push_back(j);
+  for (int j = 0; j < cols; ++j) (rem[j] < K ? small : large).push_back(j);
   while (!small.empty() && !large.empty()) {
     const int s = small.front();
     small.pop_front();
     const int l = large.front();
     T[s] = rem[s];
-    alias[s] = (uint8_t)l;
+    alias[s] = (uint16_t)l;
     rem[l] -= K - rem[s];
     if (rem[l] < K) {
       large.pop_front();
@@ -113,23 +113,25 @@ void vose(const std::vector<uint64_t>& q, uint64_t T[256], uint8_t alias[256]) {
   }
   for (int l : large) {
     T[l] = K;
-    alias[l] = (uint8_t)l;
+    alias[l] = (uint16_t)l;
   }
   for (int s : small) {
     T[s] = K;
-    alias[s] = (uint8_t)s;
+    alias[s] = (uint16_t)s;
   }
 }
 
-int build_one(int dist, zig_tables_export* out) {
+// Tables of dist for i_max = 2^ibits (ibits 8 or 10).
+int build_one(int dist, int ibits, zig_tables_ex* out) {
   std::memset(out, 0, sizeof(*out));
+  const int imax = 1 << ibits;
   const Density P(dist);
-  const quad area = (quad)1 / 256;
-  quad X[257], F[257];  // abscissae and normalised heights
+  const quad area = (quad)1 / imax;
+  std::vector<quad> X(imax + 1), F(imax + 1);  // abscissae and normalised heights
   int L = 0;
   quad fprev = 0;
-  quad xprev = dist == ZIG_EXP ? (quad)64 : (quad)40;  // area << 1/256 there
-  for (int k = 0; k < 256; ++k) {
+  quad xprev = dist == ZIG_EXP ? (quad)64 : (quad)40;  // area << 1/i_max there
+  for (int k = 0; k < imax; ++k) {
     // area of the layer with corner at x and bottom fprev, and derivatives
     auto g = [&](quad x) { return x * (P.p(x) - fprev); };
     auto g1 = [&](quad x) { return P.p(x) - fprev + x * P.dp(x); };
@@ -150,15 +152,16 @@ int build_one(int dist, zig_tables_export* out) {
   F[L] = P.p(0);
 
   // Masses: tail beyond X_0, then overhang j = 1..L (j = L is the cap).
-  quad A[257];
+  std::vector<quad> A(L + 1);
   A[0] = P.tail(X[0]);
   for (int j = 1; j <= L; ++j)
     A[j] = P.mass(X[j], X[j - 1]) - F[j - 1] * (X[j - 1] - X[j]);
 
   out->dist = dist;
   out->L = L;
-  out->imax = 256;
-  quad H[257];
+  out->imax = imax;
+  out->index_bits = ibits;
+  std::vector<quad> H(L + 1);
   for (int k = 0; k <= L; ++k) H[k] = (k == L) ? (quad)1 : P.height(X[k]);
   for (int k = 0; k <= L; ++k) {
     out->X[k] = (double)X[k];
@@ -193,10 +196,10 @@ int build_one(int dist, zig_tables_export* out) {
     out->tau = round_down((quad)1 - emax * ((quad)1 + ldexpf128((quad)1, -40)));
   }
 
-  // Integer alias weights, total 2^64 (256 columns of capacity 2^56).
+  // Integer alias weights, total 2^64 (i_max columns of capacity 2^64 / i_max).
   quad sum = 0;
   for (int j = 0; j <= L; ++j) sum += A[j];
-  std::vector<uint64_t> q(256, 0);
+  std::vector<uint64_t> q(imax, 0);
   const quad scale = ldexpf128((quad)1, 64);
   unsigned __int128 tot = 0;
   int imax_w = 0;
@@ -210,15 +213,52 @@ int build_one(int dist, zig_tables_export* out) {
     q[imax_w] -= (uint64_t)(tot - want);
   else
     q[imax_w] += (uint64_t)(want - tot);
-  vose(q, out->T, out->alias);
+  vose(q, imax, (uint64_t)1 << (64 - ibits), out->T, out->alias);
   return 0;
+}
+
+// The 256-column tables in the original export layout.
+void narrow(const zig_tables_ex& w, zig_tables_export* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->dist = w.dist;
+  out->L = w.L;
+  out->imax = w.imax;
+  for (int k = 0; k < 257; ++k) {
+    out->X[k] = w.X[k];
+    out->f[k] = w.f[k];
+    out->dX[k] = w.dX[k];
+    out->df[k] = w.df[k];
+    out->A[k] = w.A[k];
+    out->X32[k] = w.X32[k];
+    out->f32[k] = w.f32[k];
+    out->dX32[k] = w.dX32[k];
+    out->df32[k] = w.df32[k];
+  }
+  out->eps = w.eps;
+  out->tau = w.tau;
+  out->rinv = w.rinv;
+  out->rinv32 = w.rinv32;
+  for (int c = 0; c < 256; ++c) {
+    out->T[c] = w.T[c];
+    out->alias[c] = (uint8_t)w.alias[c];
+  }
 }
 
 }  // namespace
 
 int build_host_tables(zig_tables_export* exp_tab, zig_tables_export* nrm_tab) {
-  if (build_one(ZIG_EXP, exp_tab) != 0) return 1;
-  if (build_one(ZIG_NORMAL, nrm_tab) != 0) return 1;
+  static zig_tables_ex w;  // ~55 KB: not on the stack
+  if (build_one(ZIG_EXP, 8, &w) != 0) return 1;
+  narrow(w, exp_tab);
+  if (build_one(ZIG_NORMAL, 8, &w) != 0) return 1;
+  narrow(w, nrm_tab);
+  return 0;
+}
+
+int build_host_tables_ex(int ibits, zig_tables_ex* exp_tab, zig_tables_ex* nrm_tab) {
+  if (ibits != 8 && ibits != 10) return 1;
+  if (build_one(ZIG_EXP, ibits, exp_tab) != 0) return 1;
+  if (build_one(ZIG_NORMAL, ibits, nrm_tab) != 0) return 1;
   return 0;
 }
 

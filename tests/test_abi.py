@@ -151,3 +151,25 @@ def test_tune_cache_roundtrip(zig, tmp_path):
     assert a["gsamples_s"] == pytest.approx(2.5)
     with pytest.raises(zig.ZigError):
         zig.zig_tune_load(str(tmp_path / "missing.jsonl"))
+
+
+@pytest.mark.parametrize("bits", [8, 10])
+@pytest.mark.parametrize("dist", [0, 1])
+def test_wide_tables_equal_oracle_tables(zig, orc, dist, bits):
+    """The library's tables at both index widths (i_max 256 and 1024) equal
+    the oracle's entry for entry."""
+    t = zig.zig_export_tables_ex(dist, bits)
+    r = orc.tables(dist, bits, 52, 64 - bits)
+    assert (t.imax, t.index_bits, t.L) == (r.imax, bits, r.L)
+    L, M = t.L, t.imax
+    for name in ("X", "f", "dX", "df", "X32", "f32", "dX32", "df32"):
+        a = np.ctypeslib.as_array(getattr(t, name))[: L + 1]
+        b = np.ctypeslib.as_array(getattr(r, name))[: L + 1]
+        assert np.array_equal(a, b), name
+    assert np.allclose(np.ctypeslib.as_array(t.A)[: L + 1], np.ctypeslib.as_array(r.A)[: L + 1],
+                       rtol=1e-15, atol=0)
+    assert (t.eps, t.tau, t.rinv, t.rinv32) == (r.eps, r.tau, r.rinv, r.rinv32)
+    assert list(t.T)[:M] == list(r.T)[:M]
+    assert list(t.alias)[:M] == list(r.alias)[:M]
+    with pytest.raises(zig.ZigError):
+        zig.zig_export_tables_ex(dist, 9)
