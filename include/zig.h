@@ -144,6 +144,18 @@ typedef struct zig_tables_ex {
   float reserved;
   uint64_t T[1024];
   uint16_t alias[1024];
+  /* Per-box shortcut bounds of the overhang test, box j = 1..L, on the
+   * integer sum mx + my of the two uniforms (mx = ux 2^52 for FP64, 2^23 for
+   * FP32): a point below acc lies under the curve, one above rej over it,
+   * each with a margin for the rounding of x, y and exp, so that skipping
+   * the exact test never changes its answer (for the exponential acc also
+   * covers the always-accept region ux + uy < tau of Sec. 2).  These bounds
+   * give the per-overhang eps of Appendix D item 2 and the normal's
+   * convex/concave regions; the outputs are those of the exact test. */
+  uint64_t acc52[1025];
+  uint64_t rej52[1025];
+  uint64_t acc23[1025];
+  uint64_t rej23[1025];
 } zig_tables_ex;
 
 /*

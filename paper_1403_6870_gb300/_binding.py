@@ -89,6 +89,8 @@ class zig_tables_ex(ctypes.Structure):
         ("dX32", ctypes.c_float * 1025), ("df32", ctypes.c_float * 1025),
         ("rinv32", ctypes.c_float), ("reserved", ctypes.c_float),
         ("T", ctypes.c_uint64 * 1024), ("alias", ctypes.c_uint16 * 1024),
+        ("acc52", ctypes.c_uint64 * 1025), ("rej52", ctypes.c_uint64 * 1025),
+        ("acc23", ctypes.c_uint64 * 1025), ("rej23", ctypes.c_uint64 * 1025),
     ]
 
 

@@ -42,9 +42,11 @@ struct DevTabT {
   float df32[kIMax + 1];
   unsigned long long T[kIMax];  // alias thresholds (scale 2^(64 - IB))
   typename std::conditional<(IB <= 8), unsigned char, unsigned short>::type alias[kIMax];
+  // per-box bounds on mx + my: under the curve below acc, over it above rej
+  // (exponential: acc covers the always-accept region ux + uy < tau)
+  unsigned long long acc52[kIMax + 1], rej52[kIMax + 1];
+  unsigned int acc23[kIMax + 1], rej23[kIMax + 1];
   double tau;                  // exponential always-accept bound on ux + uy
-  unsigned long long thr52;    // smallest integer >= tau 2^52
-  unsigned int thr23;          // smallest integer >= tau 2^23
   double rinv;                 // RN64(1 / X_0)
   float rinv32;
   int L;
@@ -278,7 +280,9 @@ struct Prec<double> {
   template <class Tab>
   static __device__ __forceinline__ double rinv(const Tab& t) { return t.rinv; }
   template <class Tab>
-  static __device__ __forceinline__ UInt thr(const Tab& t) { return t.thr52; }
+  static __device__ __forceinline__ UInt acc(const Tab& t, int j) { return t.acc52[j]; }
+  template <class Tab>
+  static __device__ __forceinline__ UInt rej(const Tab& t, int j) { return t.rej52[j]; }
   static __device__ __forceinline__ double nan() {
     return __longlong_as_double(0x7FF8000000000000ll);
   }
@@ -310,7 +314,9 @@ struct Prec<float> {
   template <class Tab>
   static __device__ __forceinline__ float rinv(const Tab& t) { return t.rinv32; }
   template <class Tab>
-  static __device__ __forceinline__ UInt thr(const Tab& t) { return t.thr23; }
+  static __device__ __forceinline__ UInt acc(const Tab& t, int j) { return t.acc23[j]; }
+  template <class Tab>
+  static __device__ __forceinline__ UInt rej(const Tab& t, int j) { return t.rej23[j]; }
   static __device__ __forceinline__ float nan() { return __int_as_float(0x7FC00000); }
 };
 
@@ -345,6 +351,12 @@ constexpr float kPreTestMargin = 1.0f / 16384.0f;
 // 5); below the chord by more than eps they are accepted without a test
 // (Sec. 2, three regions); the rest get the exact test y < e^-x.  Normal:
 // the exact test y < e^{-x^2/2}.  On accept x = X_j + ux (X_{j-1} - X_j).
+// Before the exact test, the box's own bounds on mx + my (zig.h,
+// zig_tables_ex) settle points that lie clearly under or over the curve:
+// the per-box eps of Appendix D item 2 for the exponential, and for the
+// normal the chord test on either side, which sorts the convex boxes
+// (x > 1) and the concave ones (x < 1).  They carry a rounding margin, so
+// the answer is the exact test's.
 template <int DIST, typename T, class Tab>
 __device__ __forceinline__ bool overhang_attempt(const Tab& t, int j,
                                                  typename Prec<T>::UInt mx,
@@ -356,10 +368,14 @@ __device__ __forceinline__ bool overhang_attempt(const Tab& t, int j,
       mx = nx;
       my = ny;
     }
-    if (mx + my < P::thr(t)) {
+  }
+  {
+    const typename P::UInt sum = mx + my;
+    if (sum < P::acc(t, j)) {
       x = P::fmat(P::val(mx), P::dX(t, j), P::X(t, j));
       return true;
     }
+    if (DIST != ZIG_EXP && sum > P::rej(t, j)) return false;
   }
   // FP32 view of x and y for the pre-test
   const float ux = approx_u<T>(mx), uy = approx_u<T>(my);

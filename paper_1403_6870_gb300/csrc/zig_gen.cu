@@ -837,11 +837,13 @@ void to_device_layout(const Host& h, DevTabT<IB>* d) {
     d->T[c] = h.T[c];
     d->alias[c] = h.alias[c];
   }
+  for (int j = 0; j <= h.L && j <= kIMax; ++j) {
+    d->acc52[j] = h.acc52[j];
+    d->rej52[j] = h.rej52[j];
+    d->acc23[j] = (unsigned int)h.acc23[j];
+    d->rej23[j] = (unsigned int)h.rej23[j];
+  }
   d->tau = h.tau;
-  // smallest integers m with m >= tau 2^52 (2^23): ux + uy < tau holds
-  // exactly when the integer sum of the two uniforms is below them
-  d->thr52 = (unsigned long long)std::ceil(std::ldexp(h.tau, 52));
-  d->thr23 = (unsigned int)std::ceil(std::ldexp(h.tau, 23));
   d->rinv = h.rinv;
   d->rinv32 = h.rinv32;
   d->L = h.L;
@@ -1167,8 +1169,8 @@ zig_status zig_build_tables(void) {
   if (g_dev[dev].ready.load()) return ZIG_OK;
   static DevTab h[2];
   static DevTabT<10> h10[2];
-  to_device_layout(g_host[0], &h[0]);
-  to_device_layout(g_host[1], &h[1]);
+  to_device_layout(g_host8ex[0], &h[0]);
+  to_device_layout(g_host8ex[1], &h[1]);
   to_device_layout(g_host10[0], &h10[0]);
   to_device_layout(g_host10[1], &h10[1]);
   void* status = nullptr;

@@ -15,6 +15,11 @@ int build_host_tables(zig_tables_export* exp_tab, zig_tables_export* nrm_tab);
 // The same at i_max = 2^ibits (ibits 8 or 10) in the wide layout.
 int build_host_tables_ex(int ibits, zig_tables_ex* exp_tab, zig_tables_ex* nrm_tab);
 
+// Per-box shortcut bounds of the overhang test (zig_tables.cpp): fills
+// t->acc52, rej52, acc23, rej23 for box j = 1..L (see zig.h); for the
+// exponential acc is at least the always-accept bound of tau.
+int box_shortcuts(int dist, zig_tables_ex* t);
+
 // Host tables, built once per process (zig_gen.cu).
 const zig_tables_export* host_tables(int dist);
 

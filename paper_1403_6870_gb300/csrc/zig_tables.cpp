@@ -255,10 +255,100 @@ int build_host_tables(zig_tables_export* exp_tab, zig_tables_export* nrm_tab) {
   return 0;
 }
 
+namespace {
+
+// Largest value of the smooth function g on [0, 1]: the best of a uniform
+// grid, refined by golden-section search around it.
+template <class G>
+quad max_on_unit(G g) {
+  const int N = 2048;
+  int best = 0;
+  quad bv = g((quad)0);
+  for (int k = 1; k <= N; ++k) {
+    const quad v = g((quad)k / N);
+    if (v > bv) {
+      bv = v;
+      best = k;
+    }
+  }
+  quad a = (quad)(best > 0 ? best - 1 : 0) / N, b = (quad)(best < N ? best + 1 : N) / N;
+  const quad r = (sqrtf128((quad)5) - 1) / 2;
+  quad c = b - r * (b - a), d = a + r * (b - a);
+  quad gc = g(c), gd = g(d);
+  for (int it = 0; it < 120; ++it) {
+    if (gc > gd) {
+      b = d;
+      d = c;
+      gd = gc;
+      c = b - r * (b - a);
+      gc = g(c);
+    } else {
+      a = c;
+      c = d;
+      gc = gd;
+      d = a + r * (b - a);
+      gd = g(d);
+    }
+  }
+  const quad m = gc > gd ? gc : gd;
+  return m > bv ? m : bv;
+}
+
+// Shortcut bounds of one box at one precision (b bits of U).  X, dX, f0
+// (= f_{j-1}) and df are the rounded table values the device uses; the
+// curve h is exact.  In box coordinates (ux, uy) in [0, 1)^2 the curve is
+// uy_c(ux) = (h(X + ux dX) - f0) / df; Dm and Dp are the largest distances
+// of the curve below and above the chord uy = 1 - ux.  A point with
+// ux + uy < 1 - Dm - margin lies under the curve, one with
+// ux + uy > 1 + Dp + margin above it, with a margin that exceeds what the
+// rounding of x and y to the precision and of exp can move the exact test
+// y < h(x).  Returns the integer bounds on mx + my (mx = ux 2^b): accept
+// when below acc, reject when above rej.
+void box_bounds(int dist, quad X, quad dX, quad f0, quad df, int b, uint64_t* acc, uint64_t* rej) {
+  auto h = [&](quad x) { return dist == ZIG_EXP ? expf128(-x) : expf128(-(x * x) / 2); };
+  auto dev = [&](quad u) { return (h(X + u * dX) - f0) / df - (1 - u); };
+  const quad Dp = max_on_unit(dev);
+  const quad Dm = max_on_unit([&](quad u) { return -dev(u); });
+  // rounding of x and y to b + 1 significant bits, of the FP64 exp, and the
+  // refinement error: in box-height units, with a factor 8 to spare
+  const quad ulp_y = ldexpf128((quad)1, -(b + 1)) * (f0 + df);
+  const quad xmax = X + dX;
+  const quad slope = dist == ZIG_EXP ? h(X) : (X > 1 ? X * h(X) : (xmax > 1 ? expf128((quad)-0.5) : xmax * h(xmax)));
+  const quad ulp_x = ldexpf128((quad)1, -(b + 1)) * xmax;
+  const quad r = (ulp_y + slope * ulp_x + ldexpf128((quad)1, -50) * (f0 + df)) / df;
+  const quad margin = 8 * r + ldexpf128((quad)1, -(b - 4));
+  const quad scale = ldexpf128((quad)1, b);
+  const quad lo = (1 - (Dm > 0 ? Dm : 0) - margin) * scale;
+  const quad hi = (1 + (Dp > 0 ? Dp : 0) + margin) * scale;
+  *acc = lo > 0 ? (uint64_t)floorf128(lo) : 0;
+  *rej = (uint64_t)ceilf128(hi);
+}
+
+}  // namespace
+
+int box_shortcuts(int dist, zig_tables_ex* t) {
+  for (int j = 0; j <= t->imax; ++j) t->acc52[j] = t->rej52[j] = t->acc23[j] = t->rej23[j] = 0;
+  // the always-accept bound of Sec. 2 (exponential): smallest integers at or
+  // above tau 2^52 and tau 2^23
+  const uint64_t thr52 = dist == ZIG_EXP ? (uint64_t)ceil(ldexp(t->tau, 52)) : 0;
+  const uint64_t thr23 = dist == ZIG_EXP ? (uint64_t)ceil(ldexp(t->tau, 23)) : 0;
+  for (int j = 1; j <= t->L; ++j) {
+    box_bounds(dist, (quad)t->X[j], (quad)t->dX[j], (quad)t->f[j - 1], (quad)t->df[j], 52,
+               &t->acc52[j], &t->rej52[j]);
+    box_bounds(dist, (quad)t->X32[j], (quad)t->dX32[j], (quad)t->f32[j - 1], (quad)t->df32[j], 23,
+               &t->acc23[j], &t->rej23[j]);
+    if (t->acc52[j] < thr52) t->acc52[j] = thr52;
+    if (t->acc23[j] < thr23) t->acc23[j] = thr23;
+  }
+  return 0;
+}
+
 int build_host_tables_ex(int ibits, zig_tables_ex* exp_tab, zig_tables_ex* nrm_tab) {
   if (ibits != 8 && ibits != 10) return 1;
   if (build_one(ZIG_EXP, ibits, exp_tab) != 0) return 1;
   if (build_one(ZIG_NORMAL, ibits, nrm_tab) != 0) return 1;
+  box_shortcuts(ZIG_EXP, exp_tab);
+  box_shortcuts(ZIG_NORMAL, nrm_tab);
   return 0;
 }
 
