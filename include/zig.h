@@ -176,16 +176,20 @@ zig_status zig_export_tables(zig_dist dist, zig_tables_export* h_out);
  * zig_exponential -- n standard exponential variates, Exp(1), into out.
  * zig_normal      -- n standard normal variates, N(0, 1), into out.
  *
- * Table 1 (modified column) with the readings stated above.  out is a
- * device array of n float (ZIG_F32) or double (ZIG_F64) elements, aligned
- * to its element size (any further alignment is handled internally);
- * out[t] is the variate for counter offset + t.  n = 0 is a no-op.
+ * Table 1 (modified column) with the readings stated above.  out is an
+ * array of n float (ZIG_F32) or double (ZIG_F64) elements, aligned to its
+ * element size (any further alignment is handled internally), in device or
+ * managed memory of the current device, or in page-locked host memory
+ * (cudaHostAlloc, cudaHostRegister), which the kernel then writes directly
+ * over the host link (NVLink-C2C on Grace systems); other memory (pageable
+ * host memory, another device's memory) gives ZIG_E_INVAL.  out[t] is the
+ * variate for counter offset + t.  n = 0 is a no-op.
  * FP64: fast-path outputs are the correctly rounded U * X_i.  FP32: the
  * same words, binary32 arithmetic and tables; accept/reject comparisons are
  * made exactly in binary64 against a binary64 exp.
- * Returns ZIG_OK, ZIG_E_INVAL (NULL out with n > 0, bad dtype),
- * ZIG_E_ALIGN, ZIG_E_RANGE (offset + n > 2^64), ZIG_E_NOTINIT or
- * ZIG_E_CUDA (launch failure).
+ * Returns ZIG_OK, ZIG_E_INVAL (NULL out with n > 0, bad dtype, memory the
+ * kernel cannot write), ZIG_E_ALIGN, ZIG_E_RANGE (offset + n > 2^64),
+ * ZIG_E_NOTINIT or ZIG_E_CUDA (launch failure).
  */
 zig_status zig_exponential(void* out, uint64_t n, uint64_t seed,
                            uint64_t offset, zig_dtype dtype, void* stream);

@@ -129,10 +129,14 @@ def _check(st: int, where: str) -> None:
 
 def _stream_handle(stream, tensor=None):
     if stream is None:
-        if tensor is not None and hasattr(tensor, "device"):
+        if tensor is not None and hasattr(tensor, "device") and tensor.is_cuda:
             import torch
 
             return torch.cuda.current_stream(tensor.device).cuda_stream
+        if tensor is not None and hasattr(tensor, "device"):
+            import torch
+
+            return torch.cuda.current_stream().cuda_stream
         return 0
     if hasattr(stream, "cuda_stream"):
         return stream.cuda_stream
@@ -144,8 +148,8 @@ def _out_args(out, n, dtype):
     if hasattr(out, "data_ptr"):
         import torch
 
-        if not out.is_cuda:
-            raise ValueError("out must be a CUDA tensor")
+        if not (out.is_cuda or out.is_pinned()):
+            raise ValueError("out must be a CUDA tensor or a pinned host tensor")
         if not out.is_contiguous():
             raise ValueError("out must be contiguous")
         code = {torch.float32: ZIG_F32, torch.float64: ZIG_F64}.get(out.dtype)

@@ -1057,6 +1057,34 @@ void apply_cached(int dev) {
     }
 }
 
+// The address the kernels write through: device memory of the current
+// device and managed memory as given; page-locked host memory
+// (cudaHostAlloc, cudaHostRegister) through its device alias, which the
+// kernels then write over the host link; anything else (unregistered host
+// memory, another device's memory) is refused.
+zig_status device_address(void* out, int dev, void** dptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, out) != cudaSuccess) {
+    cudaGetLastError();
+    return ZIG_E_INVAL;
+  }
+  switch (a.type) {
+    case cudaMemoryTypeDevice:
+      if (a.device != dev) return ZIG_E_INVAL;
+      *dptr = out;
+      return ZIG_OK;
+    case cudaMemoryTypeManaged:
+      *dptr = out;
+      return ZIG_OK;
+    case cudaMemoryTypeHost:
+      if (a.devicePointer == nullptr) return ZIG_E_INVAL;
+      *dptr = a.devicePointer;
+      return ZIG_OK;
+    default:
+      return ZIG_E_INVAL;
+  }
+}
+
 zig_status generate(int dist, void* out, uint64_t n, uint64_t seed, uint64_t offset,
                     zig_dtype dtype, void* stream, int keying = ZIG_KEY_INDEX,
                     int index_bits = 8) {
@@ -1076,6 +1104,9 @@ zig_status generate(int dist, void* out, uint64_t n, uint64_t seed, uint64_t off
   zig_status st = current_device(&dev);
   if (st != ZIG_OK) return st;
   if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
+  st = device_address(out, dev, &out);
+  if (st != ZIG_OK) return st;
+  if ((uintptr_t)out % es != 0) return ZIG_E_ALIGN;
   cudaStream_t s = (cudaStream_t)stream;
   if (index_bits == 10) {
     if (keying == ZIG_KEY_PACKED)
