@@ -59,7 +59,7 @@ typedef enum zig_status {
   ZIG_E_RANGE = 6,      /* offset + n wraps past 2^64, or size too large */
   ZIG_E_LOOP_LIMIT = 7, /* device: a fringe loop reached its cap */
   ZIG_E_TABLE = 8,      /* host table construction failed */
-  ZIG_E_TIMEOUT = 9     /* device: an internal wait exceeded its limit */
+  ZIG_E_TIMEOUT = 9     /* device: a bounded internal wait gave up (reserved) */
 } zig_status;
 
 typedef enum zig_dtype { ZIG_F32 = 0, ZIG_F64 = 1 } zig_dtype;
@@ -306,9 +306,10 @@ zig_status zig_batch(const zig_request* d_reqs, uint32_t count,
  * Synchronises stream first.  Returns ZIG_OK if no device-side condition
  * was recorded since the last poll, ZIG_E_LOOP_LIMIT if a fringe loop hit
  * its cap (those outputs are NaN), ZIG_E_INVAL if zig_batch skipped an
- * invalid request, ZIG_E_TIMEOUT if a kernel's internal
- * wait between its warps gave up after 20 s (its outputs are then
- * incomplete), ZIG_E_NOTINIT or ZIG_E_CUDA.
+ * invalid request, ZIG_E_NOTINIT or ZIG_E_CUDA.  ZIG_E_TIMEOUT is
+ * reserved for a bounded device-side wait that gives up; the current
+ * kernels have no wait between warps or CTAs that could (the batch kernel's
+ * one bounded wait falls back to other work instead).
  */
 zig_status zig_status_poll(void* stream);
 

@@ -23,7 +23,6 @@ namespace zig {
 
 constexpr int kBatchReqBits = 23;  // requests per batch: below 2^23
 constexpr int kBatchPosBits = 40;  // variates per request: below 2^40
-constexpr uint64_t kBatchPosMask = (1ull << kBatchPosBits) - 1ull;
 constexpr unsigned kBatchInvalidBit = 1u << 10;  // status bit: a request was rejected
 
 // Per-request derived state (workspace).

@@ -89,7 +89,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kPThreads = kThreads;          // threads making outputs per CTA (all)
 constexpr int kQueue = 64;                   // fringe queue slots per warp
 constexpr uint64_t kWholeTag = 1ull << 63;   // position needs the whole sampler
-constexpr unsigned kWaitBit = 1u << 9;       // status bit: a bounded wait gave up
+constexpr unsigned kWaitBit = 1u << 9;       // status bit: a bounded wait gave up (reserved)
 
 // V elements per vector store, R vector stores per producer thread per tile.
 // A generation shape: V-element vectors (one vector store each), R vectors
@@ -129,12 +129,6 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
-  return *(const volatile unsigned*)p;
-}
-__device__ __forceinline__ uint64_t ld_volatile(const uint64_t* p) {
-  return *(const volatile uint64_t*)p;
-}
 __device__ __forceinline__ double ld_volatile_d(const double* p) {
   return *(const volatile double*)p;
 }
