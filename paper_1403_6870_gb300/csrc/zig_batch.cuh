@@ -240,6 +240,11 @@ __device__ __forceinline__ uint32_t find_request(const BatchReq* reqs, uint32_t 
   return lo;
 }
 
+// The batch's tile shape: the default one without interleaved vectors (the
+// batch kernel's register budget is set for 2 CTAs per SM; measured).
+template <typename T>
+using BatchShape = Shape<GenShape<T>::V, GenShape<T>::R, GenShape<T>::MB, 1>;
+
 // One session: tiles [t0, t1) of request r, by the whole CTA, class known
 // at compile time.  On return this thread's warp has finished its outputs
 // of the session (the warps have not synchronised).
@@ -257,7 +262,7 @@ __device__ ZIG_BATCH_RUN_ATTR void batch_run(BatchCtaState& sh, const BatchReq* 
   sink.b = sizeof(T) == 8 ? (T)q.b64 : (T)q.b32;
   const uint64_t seed = q.seed, tile0 = q.tile0;
   const RoundKeys rk = device_keys(seed);
-  gen_tiles<DIST, T, GenShape<T>, 0, 8>(sh, sink, batch_sx<T>(sh, DIST), q.n, q.head, q.nvec, seed,
+  gen_tiles<DIST, T, BatchShape<T>, 0, 8>(sh, sink, batch_sx<T>(sh, DIST), q.n, q.head, q.nvec, seed,
                                      q.offset, rk, lim, t0 - tile0, t1 - tile0, 1, t0 == tile0);
 }
 

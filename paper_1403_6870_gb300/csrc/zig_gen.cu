@@ -97,9 +97,10 @@ constexpr unsigned kWaitBit = 1u << 9;       // status bit: a bounded wait gave 
 // the CTAs per SM the register budget is compiled for.  The outputs do not
 // depend on the shape: element t is always the variate of counter
 // offset + t.
-template <int V_, int R_, int MB_>
+template <int V_, int R_, int MB_, int U_ = 0>
 struct Shape {
-  static constexpr int V = V_, R = R_, MB = MB_;
+  // U: vectors whose Philox chains are interleaved (0: the precision's default)
+  static constexpr int V = V_, R = R_, MB = MB_, U = U_;
 };
 
 // Default shapes (the batch and fused kernels use these).
@@ -112,7 +113,8 @@ struct GenShape<float> : Shape<ZIG_GEN_V32, ZIG_GEN_R32, ZIG_GEN_MINBLOCKS> {};
 
 // Default shapes of packed keying: a Philox block makes 2 FP64 / 4 FP32
 // outputs, so an FP32 thread makes 64 outputs per tile to spread the tile's
-// fixed costs (measured on GB300 against R = 2 and 4).
+// fixed costs, with the register budget of 2 CTAs per SM (measured on GB300
+// against R = 2 and 4 and 3 CTAs per SM).
 #ifndef ZIG_PACKED_R32
 #define ZIG_PACKED_R32 8
 #endif
@@ -120,8 +122,11 @@ template <typename T>
 struct PackedShape;
 template <>
 struct PackedShape<double> : Shape<ZIG_GEN_V64, ZIG_GEN_R64, ZIG_GEN_MINBLOCKS> {};
+#ifndef ZIG_PACKED_MB32
+#define ZIG_PACKED_MB32 2
+#endif
 template <>
-struct PackedShape<float> : Shape<ZIG_GEN_V32, ZIG_PACKED_R32, ZIG_GEN_MINBLOCKS> {};
+struct PackedShape<float> : Shape<ZIG_GEN_V32, ZIG_PACKED_R32, ZIG_PACKED_MB32> {};
 
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
@@ -453,10 +458,14 @@ __device__ __forceinline__ int mask_popc(unsigned long long m) { return __popcll
 __device__ __forceinline__ int mask_ffs(unsigned m) { return __ffs(m); }
 __device__ __forceinline__ int mask_ffs(unsigned long long m) { return __ffsll(m); }
 
-#ifndef ZIG_GEN_UNROLL_R
-#define ZIG_GEN_UNROLL_R 1
+// Vectors of a thread's tile whose Philox chains are interleaved (unrolled):
+// FP64 2, FP32 1 (measured on GB300; more only raises register pressure).
+#ifndef ZIG_GEN_UNROLL_R64
+#define ZIG_GEN_UNROLL_R64 2
 #endif
-constexpr int kUnrollR = ZIG_GEN_UNROLL_R;
+#ifndef ZIG_GEN_UNROLL_R32
+#define ZIG_GEN_UNROLL_R32 1
+#endif
 #ifndef ZIG_PACKED_UNROLL_R
 #define ZIG_PACKED_UNROLL_R 4
 #endif
@@ -474,6 +483,8 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
     Sink& sink, uint64_t g0, uint64_t v0, uint64_t nvec, bool full, const RoundKeys& rk,
     const T* sX, uint32_t L) {
   constexpr int V = Shp::V, R = Shp::R;
+  constexpr int kUnrollR =
+      Shp::U > 0 ? Shp::U : (sizeof(T) == 8 ? ZIG_GEN_UNROLL_R64 : ZIG_GEN_UNROLL_R32);
   static_assert(V * R <= 64, "at most 64 outputs per thread and tile");
   FringeMask<V * R> fm = 0;
   const RunState run(g0, rk);
