@@ -91,9 +91,9 @@ constexpr int kQueue = 64;                   // fringe queue slots per warp
 constexpr uint64_t kWholeTag = 1ull << 63;   // position needs the whole sampler
 constexpr unsigned kWaitBit = 1u << 9;       // status bit: a bounded wait gave up (reserved)
 
-// V elements per vector store, R vector stores per producer thread per tile.
+// V elements per vector store, R vector stores per thread per tile.
 // A generation shape: V-element vectors (one vector store each), R vectors
-// per producer thread and tile (S = V R outputs per thread and tile), and
+// per thread and tile (S = V R outputs per thread and tile), and
 // the CTAs per SM the register budget is compiled for.  The outputs do not
 // depend on the shape: element t is always the variate of counter
 // offset + t.
@@ -471,9 +471,10 @@ __device__ __forceinline__ int mask_ffs(unsigned long long m) { return __ffsll(m
 #endif
 constexpr int kPackedUnrollR = ZIG_PACKED_UNROLL_R;
 
-// Steps 1-2 for one producer thread's S = V R outputs of a tile: vector r
+// Steps 1-2 for one thread's S = V R outputs of a tile: vector r
 // holds counters g0 + r kPThreads V + [0, V) and is vector v0 + r kPThreads
-// of the output.  Only V Philox chains are live at a time.  Returns the
+// of the output.  The Philox chains of U vectors are interleaved (U from
+// the shape, else the precision's default).  Returns the
 // mask of outputs (bit r V + k) whose layer index is not below L_max.
 // NOWRAP: the low counter words do not wrap inside the run.  full: every
 // vector lies inside the output (else vector r exists only if
@@ -509,7 +510,7 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
   return fm;
 }
 
-// Packed keying (KEY 1) for one producer thread's tile: each Philox block
+// Packed keying (KEY 1) for one thread's tile: each Philox block
 // gives B = V / P whole outputs (P = 2 FP64 words or 4 FP32 lanes), so a
 // vector takes V / P blocks.  MODE 0: the vector's counters start at a
 // multiple of P and the run's block counters do not wrap their low word;
