@@ -204,10 +204,11 @@ zig_status zig_normal(void* out, uint64_t n, uint64_t seed, uint64_t offset,
  *
  * Outputs (device memory, overwritten):
  *   d_sums[k] = sum of x^(k+1), k = 0..3, accumulated per thread in the
- *     variates' precision over one tile of 16 values (FP32) or directly
- *     (FP64) and then in FP64; the draws finished by the fringe warp are
- *     added in their completion order, so the sums are reproducible to
- *     about 1e-15 relative, not bit for bit;
+ *     variates' precision over one tile of a thread's values (32 at the
+ *     default FP32 shape, 64 with packed keying) or directly (FP64) and
+ *     then in FP64; the draws finished by the fringe stages are added in
+ *     their completion order, so the sums are reproducible to about 1e-15
+ *     relative, not bit for bit;
  *   d_hist[b], b < 4098: count of variates with floor(256 x) + 2048 = b for
  *     -8 <= x < 8, b = 4096 for x < -8, b = 4097 for x >= 8 or NaN (exact).
  * d_workspace: caller-owned device scratch of at least
@@ -225,6 +226,16 @@ zig_status zig_moments(zig_dist dist, zig_dtype dtype, uint64_t n,
                        uint64_t seed, uint64_t offset, double* d_sums,
                        unsigned long long* d_hist, void* d_workspace,
                        size_t workspace_bytes, void* stream);
+
+/* zig_moments over the variates of a keying (zig_keying below): with
+ * ZIG_KEY_INDEX exactly zig_moments; with ZIG_KEY_PACKED the variates of
+ * zig_generate(dist, ZIG_KEY_PACKED, 8, ...).  The workspace size of
+ * zig_moments_workspace_bytes covers both keyings.  Returns as zig_moments,
+ * plus ZIG_E_INVAL for an unknown keying. */
+zig_status zig_moments_keyed(zig_dist dist, zig_dtype dtype, int keying, uint64_t n,
+                             uint64_t seed, uint64_t offset, double* d_sums,
+                             unsigned long long* d_hist, void* d_workspace,
+                             size_t workspace_bytes, void* stream);
 
 /*
  * zig_moments_noalloc -- zig_moments without a caller workspace.

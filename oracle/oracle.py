@@ -129,6 +129,11 @@ def lib():
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_int]
             L.orc_moments.restype = ctypes.c_int64
+            L.orc_moments_keyed.argtypes = [P(Tables), P(Tables), ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int]
+            L.orc_moments_keyed.restype = ctypes.c_int64
             L.orc_enum_overhang.argtypes = [P(Tables), ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
             L.orc_enum_overhang.restype = ctypes.c_int64
             L.orc_transform64.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -201,15 +206,17 @@ def fill(dist: int, dtype: int, seed: int, offset: int, n: int, idx=None,
     return out, int(errs), words, margin
 
 
-def moments(dist: int, dtype: int, seed: int, offset: int, n: int, nthreads: int | None = None):
-    """Exact-order (binary128) power sums, absolute power sums and histogram."""
+def moments(dist: int, dtype: int, seed: int, offset: int, n: int, nthreads: int | None = None,
+            keying: int = 0):
+    """Exact-order (binary128) power sums, absolute power sums and histogram
+    (keying 0 per index, 1 packed)."""
     te, tn = tables(EXP), tables(NORMAL)
     sums = np.zeros(4, dtype=np.float64)
     abss = np.zeros(4, dtype=np.float64)
     hist = np.zeros(4098, dtype=np.uint64)
-    errs = lib().orc_moments(ctypes.byref(te), ctypes.byref(tn), dist, dtype, seed, offset, n,
-                             sums.ctypes.data, abss.ctypes.data, hist.ctypes.data,
-                             nthreads or default_threads())
+    errs = lib().orc_moments_keyed(ctypes.byref(te), ctypes.byref(tn), dist, dtype, int(keying),
+                                   seed, offset, n, sums.ctypes.data, abss.ctypes.data,
+                                   hist.ctypes.data, nthreads or default_threads())
     return sums, abss, hist, int(errs)
 
 

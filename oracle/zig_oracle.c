@@ -760,7 +760,16 @@ int64_t orc_moments(const orc_tables* te, const orc_tables* tn, int dist,
                     int dtype, uint64_t seed, uint64_t offset, uint64_t n,
                     double sums[4], double abssums[4], uint64_t hist[4098],
                     int nthreads) {
+  return orc_moments_keyed(te, tn, dist, dtype, 0, seed, offset, n, sums, abssums, hist,
+                           nthreads);
+}
+
+int64_t orc_moments_keyed(const orc_tables* te, const orc_tables* tn, int dist,
+                          int dtype, int keying, uint64_t seed, uint64_t offset,
+                          uint64_t n, double sums[4], double abssums[4],
+                          uint64_t hist[4098], int nthreads) {
   fill_job* jb = (fill_job*)calloc(1, sizeof(fill_job));
+  jb->keying = keying;
   jb->te = te;
   jb->tn = tn;
   jb->dist = dist;

@@ -181,6 +181,11 @@ int64_t orc_moments(const orc_tables* te, const orc_tables* tn, int dist,
                     int dtype, uint64_t seed, uint64_t offset, uint64_t n,
                     double sums[4], double abssums[4], uint64_t hist[4098],
                     int nthreads);
+/* orc_moments with a choice of keying (0 per index, 1 packed). */
+int64_t orc_moments_keyed(const orc_tables* te, const orc_tables* tn, int dist,
+                          int dtype, int keying, uint64_t seed, uint64_t offset,
+                          uint64_t n, double sums[4], double abssums[4],
+                          uint64_t hist[4098], int nthreads);
 
 /* Enumerate the 2^bits x 2^bits grid (ux, uy) = (a 2^-bits, b 2^-bits),
  * the values U takes at bits-bit resolution, through

@@ -72,6 +72,8 @@ _moments = _sig("zig_moments", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp, _v
 _batch_ws = _sig("zig_batch_workspace_bytes", ctypes.c_size_t, [ctypes.c_uint32])
 _batch_validate = _sig("zig_batch_validate", _int, [_vp, ctypes.c_uint32])
 _batch = _sig("zig_batch", _int, [_vp, ctypes.c_uint32, _vp, _vp, ctypes.c_size_t, _vp])
+_moments_keyed = _sig("zig_moments_keyed", _int, [_int, _int, _int, _u64, _u64, _u64, _vp, _vp,
+                                                  _vp, ctypes.c_size_t, _vp])
 _moments_noalloc = _sig("zig_moments_noalloc", _int, [_int, _int, _u64, _u64, _u64, _vp, _vp,
                                                       _vp])
 _set_limits = _sig("zig_set_fringe_limits", _int, [_int, _int])
@@ -217,6 +219,23 @@ def zig_moments(dist: int, dtype: int, n: int, seed: int, offset: int, sums, his
     _check(_moments(int(dist), int(dtype), n, seed & (2**64 - 1), offset & (2**64 - 1),
                     sums.data_ptr(), hist.data_ptr(), workspace.data_ptr(), wbytes,
                     _stream_handle(stream, sums)), "zig_moments")
+
+
+def zig_moments_keyed(dist: int, dtype: int, keying: int, n: int, seed: int, offset: int, sums,
+                      hist, workspace, stream=None) -> None:
+    """zig_moments over the variates of a keying (ZIG_KEY_INDEX or
+    ZIG_KEY_PACKED)."""
+    import torch
+
+    if sums.dtype != torch.float64 or sums.numel() < 4 or not sums.is_cuda:
+        raise ValueError("sums must be a CUDA float64 tensor of 4 elements")
+    if hist.element_size() != 8 or hist.numel() < 4098 or not hist.is_cuda:
+        raise ValueError("hist must be a CUDA 64-bit integer tensor of 4098 elements")
+    wbytes = workspace.numel() * workspace.element_size()
+    _check(_moments_keyed(int(dist), int(dtype), int(keying), n, seed & (2**64 - 1),
+                          offset & (2**64 - 1), sums.data_ptr(), hist.data_ptr(),
+                          workspace.data_ptr(), wbytes, _stream_handle(stream, sums)),
+           "zig_moments_keyed")
 
 
 def zig_moments_noalloc(dist: int, dtype: int, n: int, seed: int, offset: int, sums, hist,

@@ -963,21 +963,22 @@ int variant_occupancy(int k, int dev) {
 }
 
 // Grid of the fused reduction on device dev (one partial per CTA).
-template <int DIST, typename T>
+template <int DIST, typename T, typename Shp = GenShape<T>, int KEY = 0>
 uint64_t moment_grid_cap(int dev) {
-  return (uint64_t)g_dev[dev].sms * (uint64_t)occupancy_blocks<DIST, T, MomentSink<T>>(dev);
+  return (uint64_t)g_dev[dev].sms *
+         (uint64_t)occupancy_blocks<DIST, T, MomentSink<T>, Shp, KEY>(dev);
 }
 
 constexpr size_t kTicketBytes = 256;  // workspace: ticket, then the partials
 
-template <int DIST, typename T>
+template <int DIST, typename T, typename Shp = GenShape<T>, int KEY = 0>
 zig_status launch_moments(uint64_t n, uint64_t seed, uint64_t offset, double* d_sums,
                           unsigned long long* d_hist, void* d_ws, size_t ws_bytes,
                           cudaStream_t stream, int dev) {
-  constexpr int V = GenShape<T>::V, R = GenShape<T>::R;
+  constexpr int V = Shp::V, R = Shp::R;
   const uint64_t nvec = n / V;
   const uint64_t tiles = (nvec + (uint64_t)kPThreads * R - 1) / ((uint64_t)kPThreads * R);
-  const uint64_t cap = moment_grid_cap<DIST, T>(dev);
+  const uint64_t cap = moment_grid_cap<DIST, T, Shp, KEY>(dev);
   uint64_t grid = tiles < cap ? tiles : cap;
   if (grid < 1) grid = 1;
   if (ws_bytes < kTicketBytes + grid * 4 * sizeof(double)) return ZIG_E_NOMEM;
@@ -989,7 +990,7 @@ zig_status launch_moments(uint64_t n, uint64_t seed, uint64_t offset, double* d_
   Limits lim{g_max_att.load(), g_max_tail.load()};
   ReduceOut red{d_sums, d_hist, (double*)((char*)d_ws + kTicketBytes), (unsigned*)d_ws};
   MomentSink<T> sink{};
-  gen_kernel<DIST, T, MomentSink<T>><<<(unsigned)grid, kThreads, 0, stream>>>(
+  gen_kernel<DIST, T, MomentSink<T>, Shp, KEY><<<(unsigned)grid, kThreads, 0, stream>>>(
       sink, n, 0u, nvec, seed, offset, round_keys(seed), lim, red);
   if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
   return ZIG_OK;
@@ -1384,19 +1385,35 @@ size_t zig_moments_workspace_bytes(zig_dist dist, zig_dtype dtype) {
   int dev;
   if (current_device(&dev) != ZIG_OK || !g_dev[dev].ready.load(std::memory_order_acquire))
     return 0;
-  uint64_t cap;
-  if (dist == ZIG_EXP)
+  // enough for either keying
+  uint64_t cap, cap2;
+  if (dist == ZIG_EXP) {
     cap = dtype == ZIG_F64 ? moment_grid_cap<ZIG_EXP, double>(dev)
                            : moment_grid_cap<ZIG_EXP, float>(dev);
-  else
+    cap2 = dtype == ZIG_F64 ? moment_grid_cap<ZIG_EXP, double, PackedShape<double>, 1>(dev)
+                            : moment_grid_cap<ZIG_EXP, float, PackedShape<float>, 1>(dev);
+  } else {
     cap = dtype == ZIG_F64 ? moment_grid_cap<ZIG_NORMAL, double>(dev)
                            : moment_grid_cap<ZIG_NORMAL, float>(dev);
+    cap2 = dtype == ZIG_F64 ? moment_grid_cap<ZIG_NORMAL, double, PackedShape<double>, 1>(dev)
+                            : moment_grid_cap<ZIG_NORMAL, float, PackedShape<float>, 1>(dev);
+  }
+  if (cap2 > cap) cap = cap2;
   return kTicketBytes + (size_t)cap * 4 * sizeof(double);
 }
 
 zig_status zig_moments(zig_dist dist, zig_dtype dtype, uint64_t n, uint64_t seed,
                        uint64_t offset, double* d_sums, unsigned long long* d_hist,
                        void* d_workspace, size_t workspace_bytes, void* stream) {
+  return zig_moments_keyed(dist, dtype, ZIG_KEY_INDEX, n, seed, offset, d_sums, d_hist,
+                           d_workspace, workspace_bytes, stream);
+}
+
+zig_status zig_moments_keyed(zig_dist dist, zig_dtype dtype, int keying, uint64_t n,
+                             uint64_t seed, uint64_t offset, double* d_sums,
+                             unsigned long long* d_hist, void* d_workspace,
+                             size_t workspace_bytes, void* stream) {
+  if (keying != ZIG_KEY_INDEX && keying != ZIG_KEY_PACKED) return ZIG_E_INVAL;
   if (dist != ZIG_EXP && dist != ZIG_NORMAL) return ZIG_E_INVAL;
   if (dtype != ZIG_F32 && dtype != ZIG_F64) return ZIG_E_INVAL;
   if (d_sums == nullptr || d_hist == nullptr || d_workspace == nullptr) return ZIG_E_INVAL;
@@ -1409,6 +1426,19 @@ zig_status zig_moments(zig_dist dist, zig_dtype dtype, uint64_t n, uint64_t seed
   if (st != ZIG_OK) return st;
   if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
   cudaStream_t s = (cudaStream_t)stream;
+  if (keying == ZIG_KEY_PACKED) {
+    if (dist == ZIG_EXP)
+      return dtype == ZIG_F64
+                 ? launch_moments<ZIG_EXP, double, PackedShape<double>, 1>(
+                       n, seed, offset, d_sums, d_hist, d_workspace, workspace_bytes, s, dev)
+                 : launch_moments<ZIG_EXP, float, PackedShape<float>, 1>(
+                       n, seed, offset, d_sums, d_hist, d_workspace, workspace_bytes, s, dev);
+    return dtype == ZIG_F64
+               ? launch_moments<ZIG_NORMAL, double, PackedShape<double>, 1>(
+                     n, seed, offset, d_sums, d_hist, d_workspace, workspace_bytes, s, dev)
+               : launch_moments<ZIG_NORMAL, float, PackedShape<float>, 1>(
+                     n, seed, offset, d_sums, d_hist, d_workspace, workspace_bytes, s, dev);
+  }
   if (dist == ZIG_EXP)
     return dtype == ZIG_F64 ? launch_moments<ZIG_EXP, double>(n, seed, offset, d_sums, d_hist,
                                                               d_workspace, workspace_bytes, s, dev)

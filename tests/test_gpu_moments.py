@@ -4,8 +4,11 @@ The variates are those of zig_normal/zig_exponential on the same counters
 (themselves checked element by element), so the oracle's plain definitions
 apply: the histogram must equal the oracle's exactly; each power sum must
 be within the rounding bound of its accumulation scheme (FP32 partials of
-at most 16 terms plus FP64 accumulation):
-|S_gpu - S| <= 20 * 2^-24 * sum |x|^k (FP32) or 1e-12 * sum |x|^k (FP64).
+at most m terms, m = 32 at the default FP32 shape and 64 with packed
+keying, plus FP64 accumulation):
+|S_gpu - S| <= (m + 4) 2^-24 sum |x|^k (FP32) or 1e-12 sum |x|^k (FP64).
+Packed keying (zig_moments_keyed) is checked against the oracle's packed
+word source the same way.
 At the full 2^34 size: moments within 5 standard errors of the closed
 forms and the histogram against the exact bin probabilities.
 """
@@ -32,25 +35,34 @@ def zig():
     return z
 
 
-def _run(z, dist, dtype, n, seed, offset):
+def _run(z, dist, dtype, n, seed, offset, keying=0):
     sums = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
     hist = torch.full((4098,), -1, dtype=torch.int64, device="cuda")
     ws = torch.empty(z.zig_moments_workspace_bytes(dist, dtype), dtype=torch.uint8, device="cuda")
-    z.zig_moments(dist, dtype, n, seed, offset, sums, hist, ws)
+    if keying:
+        z.zig_moments_keyed(dist, dtype, keying, n, seed, offset, sums, hist, ws)
+    else:
+        z.zig_moments(dist, dtype, n, seed, offset, sums, hist, ws)
     return sums.cpu().numpy(), hist.cpu().numpy().astype(np.uint64)
 
 
+def _tol(dtype, keying, abss):
+    m = 64 if keying else 32  # FP32 terms per partial sum
+    return ((m + 4) * 2.0**-24 if dtype == 0 else 1e-12) * abss + 1e-300
+
+
+@pytest.mark.parametrize("keying", [0, 1])
 @pytest.mark.parametrize("dist,dtype", [(1, 0), (0, 0), (1, 1), (0, 1)])
-def test_moments_match_oracle(zig, orc, dist, dtype):
+def test_moments_match_oracle(zig, orc, dist, dtype, keying):
     n, seed, off = (1 << 22) + 333, 0x9E3779B97F4A7C15, 4321
     for rep in range(2):  # twice: the workspace ticket must reset
-        sums, hist = _run(zig, dist, dtype, n, seed, off)
+        sums, hist = _run(zig, dist, dtype, n, seed, off, keying)
         assert zig.zig_status_poll() == zig.ZIG_OK
-        ref, abss, rhist, errs = orc.moments(dist, dtype, seed, off, n)
+        ref, abss, rhist, errs = orc.moments(dist, dtype, seed, off, n, keying=keying)
         assert errs == 0
         assert np.array_equal(hist, rhist)
         assert int(hist.sum()) == n
-        tol = (20 * 2.0**-24 if dtype == 0 else 1e-12) * abss + 1e-300
+        tol = _tol(dtype, keying, abss)
         assert np.all(np.abs(sums - ref) <= tol), (sums, ref, tol)
 
 
@@ -59,7 +71,7 @@ def test_moments_small_and_edge_sizes(zig, orc):
         sums, hist = _run(zig, 1, 0, n, W.SEED, 17)
         ref, abss, rhist, _ = orc.moments(1, 0, W.SEED, 17, n)
         assert np.array_equal(hist, rhist)
-        assert np.all(np.abs(sums - ref) <= 20 * 2.0**-24 * abss + 1e-300)
+        assert np.all(np.abs(sums - ref) <= _tol(0, 0, abss))
 
 
 def test_workspace_too_small(zig):

@@ -9,11 +9,15 @@ from fractions import Fraction
 import numpy as np
 
 
-def test_moments_and_histogram_match_plain_definitions(orc):
-    seed, off, n = 0x0123456789ABCDEF, 1000, 1 << 14
+import pytest
+
+
+@pytest.mark.parametrize("keying", [0, 1])
+def test_moments_and_histogram_match_plain_definitions(orc, keying):
+    seed, off, n = 0x0123456789ABCDEF, 1001, 1 << 14
     for dist, dtype in ((1, 0), (0, 1), (1, 1)):
-        x, errs, _, _ = orc.fill(dist, dtype, seed, off, n)
-        sums, abss, hist, e2 = orc.moments(dist, dtype, seed, off, n)
+        x, errs, _, _ = orc.fill(dist, dtype, seed, off, n, keying=keying)
+        sums, abss, hist, e2 = orc.moments(dist, dtype, seed, off, n, keying=keying)
         assert errs == 0 and e2 == 0
         xs = [Fraction(float(v)) for v in x]
         for k in range(4):
