@@ -205,6 +205,94 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fused(args):
+    """The fused workload as the bench line: each step reduces n fresh FP32
+    normals to power sums and a histogram (nothing stored)."""
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_1403_6870_gb300 as z
+
+    z.zig_build_tables()
+    c = W.WORKLOADS[args.workload]
+    n = args.n or c["n"]
+    keying = 1 if args.keying == "packed" else 0
+    stream = torch.cuda.current_stream()
+    sums = torch.zeros(4, dtype=torch.float64, device="cuda")
+    hist = torch.zeros(4098, dtype=torch.int64, device="cuda")
+    ws = torch.empty(z.zig_moments_workspace_bytes(c["dist"], c["dtype"]), dtype=torch.uint8,
+                     device="cuda")
+
+    def step(k):
+        fused_call(z, c["dist"], c["dtype"], keying, n, W.SEED,
+                   step_counter(c["offset"], k, rank, world, n), sums, hist, ws, stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(args.steps):
+            step(args.warmup + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * args.steps * world / (ms / 1e3) / 1e9
+    peak, mhz = alu_peak(z)
+    achieved = n / (ms / args.steps / 1e3) * (0.25 if keying else 1.0) * PHILOX_OPS_PER_BLOCK / 1e12
+    # e2e: the same steps with the results (sums, histogram) read to host memory
+    hs = torch.empty(4, dtype=torch.float64, pin_memory=True)
+    hh = torch.empty(4098, dtype=torch.int64, pin_memory=True)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, min(20, args.steps))
+    f0.record(stream)
+    for k in range(e2e_steps):
+        step(args.warmup + args.steps + k)
+        hs.copy_(sums, non_blocking=True)
+        hh.copy_(hist, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (Philox counters; seed 0x0123456789ABCDEF, fresh counters per step)",
+        "config": {"workload": args.workload, "dist": "normal", "n_per_step_per_gpu": n,
+                   "keying": args.keying, "l2": "nothing is stored; no flush needed",
+                   "parallelism": f"counter-range shards x{world}"},
+        "clocks": clk.summary(),
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz",
+                     "kernel": "gen_kernel<normal,float,MomentSink>",
+                     "algorithmic_ops_per_launch": n * (0.25 if keying else 1.0)
+                     * PHILOX_OPS_PER_BLOCK},
+        "e2e": {"value": n * e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * 8 + 4098 * 8},
+        "device_status": z.zig_strerror(z.zig_status_poll(stream)),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_zig(args):
     import torch
     import torch.distributed as dist
@@ -297,6 +385,7 @@ def run_zig(args):
         line["variants"] = measure_variants(z, stream)
         line["packed_keying"] = measure_packed(z, stream)
         line["i_max_1024"] = measure_i1024(z, stream)
+        line["fused"] = measure_fused(z, stream)
         del out
         torch.cuda.empty_cache()
         line["batch"] = measure_batch(z, stream)
@@ -379,6 +468,64 @@ def measure_variants(z, stream, steps: int = 100):
         res[name] = {"gsamples_s": n / (ms / 1e3) / 1e9, "gb_s": n * es / (ms / 1e3) / 1e9,
                      "ms_per_launch": ms, "launch_shape": chosen}
         del buf
+    return res
+
+
+PHILOX_OPS_PER_BLOCK = 40  # 10 rounds x (2 32x32->64 multiplies + 2 three-input XORs)
+
+
+def alu_peak(z):
+    """Lane-level instruction issue peak of the GPU: SMs x 4 schedulers x 32
+    lanes x the maximum SM clock (MEASURED_PEAKS.json sm_max_mhz, else the
+    device's)."""
+    import torch
+
+    props = torch.cuda.get_device_properties(0)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return props.multi_processor_count * 4 * 32 * mhz * 1e6 / 1e12, mhz
+
+
+def fused_call(z, dist, dtype, keying, n, seed, offset, sums, hist, ws, stream):
+    z.zig_moments_keyed(dist, dtype, keying, n, seed, offset, sums, hist, ws, stream=stream)
+
+
+def measure_fused(z, stream, reps: int = 5):
+    """The fused generate-and-reduce configuration: 2^34 FP32 normals, power
+    sums and histogram, nothing stored; per-index and packed keying.  Bound
+    by integer issue: the algorithmic work is the Philox blocks (one per
+    output per-index, one per 4 outputs packed)."""
+    import torch
+
+    c = W.WORKLOADS["normal_f32_fused_2p34"]
+    n = c["n"]
+    peak, mhz = alu_peak(z)
+    sums = torch.zeros(4, dtype=torch.float64, device="cuda")
+    hist = torch.zeros(4098, dtype=torch.int64, device="cuda")
+    ws = torch.empty(z.zig_moments_workspace_bytes(c["dist"], c["dtype"]), dtype=torch.uint8,
+                     device="cuda")
+    res = {}
+    for name, keying, blocks in (("per_index", 0, 1.0), ("packed", 1, 0.25)):
+        fused_call(z, c["dist"], c["dtype"], keying, n, W.SEED, 0, sums, hist, ws, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(reps):
+            fused_call(z, c["dist"], c["dtype"], keying, n, W.SEED, (k + 1) * n, sums, hist, ws,
+                       stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        rate = n / (ms / 1e3)
+        achieved = rate * blocks * PHILOX_OPS_PER_BLOCK / 1e12
+        res[name] = {"gsamples_s": rate / 1e9, "ms_per_launch": ms,
+                     "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                                  "unit": "Tops/s", "frac": achieved / peak}}
+    res["note"] = (f"2^34 FP32 normals reduced to 4 power sums and a 4098-bin histogram; "
+                   f"alu peak = SMs x 4 x 32 lanes x {mhz:.0f} MHz; achieved counts "
+                   f"{PHILOX_OPS_PER_BLOCK} Philox operations per block")
     return res
 
 
@@ -588,6 +735,8 @@ def main():
     args = parse_args()
     if args.batch_requests:
         run_batch_only(args)
+    elif args.impl == "zig" and "fused" in args.workload:
+        run_fused(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
