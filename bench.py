@@ -72,12 +72,14 @@ def measured_peak():
 
 
 def kernel_hash() -> str:
-    """First 16 hex digits of the SHA-256 of the generation kernel's sources
-    (zig_gen.cu followed by zig_device.cuh)."""
+    """First 16 hex digits of the SHA-256 of the generation kernel's device
+    sources: zig_gen.cu up to its host-side section, then zig_device.cuh."""
     h = hashlib.sha256()
     for path in KERNEL_SRCS:
         with open(path, "rb") as f:
-            h.update(f.read())
+            data = f.read()
+        cut = data.find(b"\n// Host side\n")
+        h.update(data if cut < 0 else data[:cut])
     return h.hexdigest()[:16]
 
 
