@@ -147,6 +147,12 @@ def lib():
                                              ctypes.c_double, ctypes.c_void_p, ctypes.c_uint64,
                                              ctypes.c_void_p, ctypes.c_int]
             L.orc_request_values.restype = ctypes.c_int64
+            L.orc_request_fast64.argtypes = [ctypes.c_int, ctypes.c_uint64, P(Tables),
+                                             ctypes.c_double, ctypes.c_double]
+            L.orc_request_fast64.restype = ctypes.c_double
+            L.orc_request_fast32.argtypes = [ctypes.c_int, ctypes.c_uint64, P(Tables),
+                                             ctypes.c_double, ctypes.c_double]
+            L.orc_request_fast32.restype = ctypes.c_float
         return _lib
 
 
@@ -283,6 +289,13 @@ def request_values(req: dict, idx) -> np.ndarray:
                              float(req["p0"]), float(req["p1"]), idx.ctypes.data, idx.size,
                              out.ctypes.data, default_threads())
     return out
+
+
+def request_fast(dist: int, dtype: int, w0: int, p0: float, p1: float) -> float:
+    """A request's fast-path value from its first word (orc_request_fast64/32)."""
+    t = tables(dist)
+    fn = lib().orc_request_fast64 if dtype == F64 else lib().orc_request_fast32
+    return float(fn(dist, w0 & (2**64 - 1), ctypes.byref(t), float(p0), float(p1)))
 
 
 def transform(dist: int, dtype: int, x: float, p0: float, p1: float) -> float:
