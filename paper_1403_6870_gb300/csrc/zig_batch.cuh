@@ -79,6 +79,9 @@ __host__ __device__ constexpr size_t batch_workspace_total(uint32_t count) {
 struct BatchCtaState {
   double sX64[2][256];
   float sX32[2][256];
+  // the session's folded fast-path tables (+-B_i, D by i | sign << 8)
+  double sB64[512], sD64[512];
+  float sB32[512], sD32[512];
   WarpQueues wq[kWarps];
 };
 
@@ -92,27 +95,34 @@ template <>
 __device__ __forceinline__ const float* batch_sx<float>(const BatchCtaState& sh, int dist) {
   return sh.sX32[dist];
 }
+__device__ __forceinline__ double* batch_sb(BatchCtaState& sh, double) { return sh.sB64; }
+__device__ __forceinline__ double* batch_sd(BatchCtaState& sh, double) { return sh.sD64; }
+__device__ __forceinline__ float* batch_sb(BatchCtaState& sh, float) { return sh.sB32; }
+__device__ __forceinline__ float* batch_sd(BatchCtaState& sh, float) { return sh.sD32; }
 
-// Sink of one request: transform, then store like StoreSink (vector vi at
-// element head + vi V, fringe outputs at their position).
+// Sink of one request: store like StoreSink (vector vi at element
+// head + vi V, fringe outputs at their position).  Step 2's values arrive
+// already mapped (kAffine: the producers use the session's sB/sD tables);
+// the fringe stages' variates are transformed here.
 template <int DIST, typename T>
 struct BatchSink {
   T* out;
   uint64_t head;
   T a, b;
+  const T* sB;
+  const T* sD;
   static constexpr bool kReduce = false;
+  static constexpr bool kAffine = true;
   __device__ __forceinline__ T tr(T x) const {
     return DIST == ZIG_EXP ? Prec<T>::mul(x, a) : Prec<T>::fmat(a, x, b);
   }
   template <int V>
   __device__ __forceinline__ void vec(uint64_t vi, const T* v, unsigned) {
-    T w[V];
-#pragma unroll
-    for (int k = 0; k < V; ++k) w[k] = tr(v[k]);
-    VecStore<T, V>::st(out + head + vi * V, w);
+    VecStore<T, V>::st(out + head + vi * V, v);
   }
   __device__ __forceinline__ void tile_end() {}
   __device__ __forceinline__ void put(uint64_t p, T x) { out[p] = tr(x); }
+  __device__ __forceinline__ void put_mapped(uint64_t p, T y) { out[p] = y; }
 };
 
 struct BatchClock {
@@ -261,6 +271,23 @@ __device__ ZIG_BATCH_RUN_ATTR void batch_run(BatchCtaState& sh, const BatchReq* 
   sink.a = sizeof(T) == 8 ? (T)q.a64 : (T)q.a32;
   sink.b = sizeof(T) == 8 ? (T)q.b64 : (T)q.b32;
   const uint64_t seed = q.seed, tile0 = q.tile0;
+  // the request's folded fast-path tables: B_i = RN(s X_i), D = RN(m -+ B_i)
+  // (exponential s = a, m = 0; normal s = sigma, m = mu; in T precision)
+  {
+    T* sB = batch_sb(sh, T());
+    T* sD = batch_sd(sh, T());
+    const T* sX = batch_sx<T>(sh, DIST);
+    for (int k = threadIdx.x; k < 512; k += kThreads) {
+      const bool neg = k >= 256;
+      const T B = Prec<T>::mul(sink.a, sX[k & 255]);
+      const T m = DIST == ZIG_EXP ? (T)0 : sink.b;
+      sB[k] = neg ? -B : B;
+      sD[k] = neg ? Prec<T>::add(m, B) : Prec<T>::add(m, -B);
+    }
+    sink.sB = sB;
+    sink.sD = sD;
+    __syncthreads();
+  }
   const RoundKeys rk = device_keys(seed);
   gen_tiles<DIST, T, BatchShape<T>, 0, 8>(sh, sink, batch_sx<T>(sh, DIST), q.n, q.head, q.nvec, seed,
                                      q.offset, rk, lim, t0 - tile0, t1 - tile0, 1, t0 == tile0);

@@ -212,6 +212,7 @@ struct StoreSink {
   T* out;
   uint64_t head;
   static constexpr bool kReduce = false;
+  static constexpr bool kAffine = false;  // step 2 returns U X_i (see BatchSink)
   template <int V>
   __device__ __forceinline__ void vec(uint64_t vi, const T* v, unsigned /*fringe*/) {
     VecStore<T, V>::st(out + head + vi * V, v);
@@ -246,6 +247,7 @@ struct MomentSink {
   double acc[4];
   T part[4];
   static constexpr bool kReduce = true;
+  static constexpr bool kAffine = false;
   __device__ __forceinline__ void init(unsigned* h) {
     hist = h;
     for (int k = 0; k < 4; ++k) {
@@ -306,6 +308,24 @@ __device__ __forceinline__ int claim(bool f, int& n) {
   return k;
 }
 
+// Step 2 with a request's affine map folded in (batched requests): with
+// sB[k] = +-B_i and sD[k] = D for k = i | sign << 8 (the normal's sign bit;
+// the exponential uses k = i), the value is RN((1 + U) sB[k] + sD[k]).
+template <int DIST>
+__device__ __forceinline__ double affine_value(uint32_t lo, uint32_t hi, const double* sB,
+                                               const double* sD) {
+  const uint32_t k = lo & (DIST == ZIG_NORMAL ? 0x1FFu : 0xFFu);
+  const double one_u = __hiloint2double((int)(0x3FF00000u | (hi >> 12)),
+                                        (int)__funnelshift_r(lo, hi, 12));
+  return __fma_rn(one_u, sB[k], sD[k]);
+}
+template <int DIST>
+__device__ __forceinline__ float affine_value(uint32_t lo, uint32_t hi, const float* sB,
+                                              const float* sD) {
+  const uint32_t k = lo & (DIST == ZIG_NORMAL ? 0x1FFu : 0xFFu);
+  return __fmaf_rn(__int_as_float((int)(0x3F800000u | (hi >> 9))), sB[k], sD[k]);
+}
+
 // Queue values.  An item is a queued value, possibly with kWholeTag (the
 // draw needs the whole sampler); the value's bits under kPosMask are the
 // output position (the batch kernel keeps a request index above them).
@@ -361,7 +381,16 @@ __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const Rou
       next = KEY == 0 ? pack(b1.z, b1.w) : 0ull;
     }
   }
-  const bool tl = active && !overhang;
+  // a sink with the affine map folded into step 2 takes a whole item's
+  // fast-path draw here, in the same form as the producers give it
+  bool fast = false;
+  if constexpr (Sink::kAffine) {
+    if (active && whole && (int)(w0 & ((1u << IB) - 1u)) < t.L) {
+      sink.put_mapped(p, affine_value<DIST>((uint32_t)w0, (uint32_t)(w0 >> 32), sink.sB, sink.sD));
+      fast = true;
+    }
+  }
+  const bool tl = active && !overhang && !fast;
   int k = claim(tl, c.tail);
   if (tl) sh.tq[k] = p;
   k = claim(retry, c.retry);
@@ -497,7 +526,10 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
     for (int k = 0; k < V; ++k) {
       const uint32_t d = (uint32_t)(r * kPThreads * V + k);
       const uint2 w = NOWRAP ? run.word(d, rk) : philox_first(g0 + d, rk);
-      v[k] = fast_value<DIST, IB>(w.x, w.y, sX);
+      if constexpr (Sink::kAffine)
+        v[k] = affine_value<DIST>(w.x, w.y, sink.sB, sink.sD);
+      else
+        v[k] = fast_value<DIST, IB>(w.x, w.y, sX);
       f |= (unsigned)((w.x & ((1u << IB) - 1u)) >= L) << k;
     }
     const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
