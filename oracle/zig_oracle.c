@@ -475,7 +475,12 @@ double orc_normal64(const orc_tables* te, const orc_tables* tn, orc_words* w,
   double U1 = u64_of(tn, w0);
   double x;
   if (i < tn->L) {
-    x = U1 * tn->X[i];
+    /* Step 2 with the sign on X_i (reading R16): RN((1 + U) sX - sX) with
+     * sX = +-X_i is +-RN(U X_i), and its zero (U = 0) is +0 for either sign;
+     * 1 + U is exact. */
+    const double sx = neg ? -tn->X[i] : tn->X[i];
+    d->words = w->used;
+    return fma(1.0 + U1, sx, -sx);
   } else {
     int j = orc_alias_pick(tn, orc_next(w));
     if (j == 0) {
@@ -575,7 +580,10 @@ float orc_normal32(const orc_tables* te, const orc_tables* tn, orc_words* w,
   float U1 = u32_of(w0);
   float x;
   if (i < tn->L) {
-    x = U1 * tn->X32[i];
+    /* as in orc_normal64 (reading R16), in binary32 */
+    const float sx = neg ? -tn->X32[i] : tn->X32[i];
+    d->words = w->used;
+    return fmaf(1.0f + U1, sx, -sx);
   } else {
     int j = orc_alias_pick(tn, orc_next(w));
     if (j == 0) {

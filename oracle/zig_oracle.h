@@ -30,7 +30,9 @@
  *   R4 reflection (ux,uy) -> (1-uy, 1-ux); R5 overhang test
  *   y = f_{j-1} + uy (f_j - f_{j-1}); R6 word layout (i = low 8 bits,
  *   normal sign = bit 8, U = top 52 bits, alias threshold = top 56 bits);
- *   R7 Philox key/counter layout; R8 deterministic integer Vose alias rule.
+ *   R7 Philox key/counter layout; R8 deterministic integer Vose alias rule;
+ *   R16 the normal's fast path rounds once with the sign on X_i,
+ *   RN((1 + U) sX - sX) for sX = +-X_i, so its zero (U = 0) is +0.
  *
  * Parity status: every function here is pinned by tests under tests/
  * (closed forms, numerical quadrature, brute-force enumeration at reduced

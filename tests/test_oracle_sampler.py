@@ -367,3 +367,25 @@ def test_distribution_ten_bit_index(orc, dist, dtype):
     assert abs(rate - p) < 5 * math.sqrt(p * (1 - p) / N_STAT)
     if dist == 1:
         assert abs(float(np.mean(x > 0)) - 0.5) < 5 * math.sqrt(0.25 / N_STAT)
+
+
+def test_fast_path_sign_and_zero(orc, te, tn):
+    # Reading R16: the normal's sign enters step 2's one rounding through
+    # +-X_i, so a negative draw is the exact negation of the positive one
+    # except at U = 0, where both signs give +0 (bit pattern 0).
+    rng = np.random.default_rng(5)
+    for dtype, it in ((orc.F64, np.uint64), (orc.F32, np.uint32)):
+        for _ in range(100):
+            i = int(rng.integers(0, tn.L))
+            m = int(rng.integers(1, 2**52))
+            if dtype == orc.F32:
+                m |= 1 << 29  # U's top 23 bits nonzero
+            pos, *_ = orc.sample_script(orc.NORMAL, [word(i, m, 0)], dtype=dtype)
+            neg, *_ = orc.sample_script(orc.NORMAL, [word(i, m, 1)], dtype=dtype)
+            assert pos > 0 and neg == -pos
+        for s in (0, 1):
+            for dist, t in ((orc.NORMAL, tn), (orc.EXP, te)):
+                x, used, over, err = orc.sample_script(dist, [word(5, 0, s if dist else 0)],
+                                                       dtype=dtype)
+                ft = np.float64 if dtype == orc.F64 else np.float32
+                assert used == 1 and np.array([x], dtype=ft).view(it)[0] == 0
