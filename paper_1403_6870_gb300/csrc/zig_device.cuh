@@ -414,7 +414,8 @@ __device__ T exp_general(W& w, const Tab& t, Limits lim, bool& err) {
     const int i = (int)(w0 & (uint64_t)(Tab::kIMax - 1));
     const typename P::UInt m1 = P::ubits(w0);
     if (i < t.L) {
-      x = P::mul(P::val(m1), P::X(t, i));
+      const T X = P::X(t, i);
+      x = P::fmat(P::one_plus(m1), X, -X);  // RN(U X_i)
       break;
     }
     const int j = alias_pick(t, w.next());
@@ -454,7 +455,9 @@ __device__ T normal_general(W& w, const Tab& te, const Tab& tn, Limits lim, bool
   const typename P::UInt m1 = P::ubits(w0);
   T x;
   if (i < tn.L) {
-    x = P::mul(P::val(m1), P::X(tn, i));
+    // the sign on X_i inside the one rounding (a zero is +0)
+    const T X = negative ? -P::X(tn, i) : P::X(tn, i);
+    return P::fmat(P::one_plus(m1), X, -X);
   } else {
     const int j = alias_pick(tn, w.next());
     if (j == 0) {
@@ -503,26 +506,25 @@ __device__ __noinline__ T sample_general(uint64_t seed, uint64_t g, Limits lim) 
 // ---------------------------------------------------------------------------
 // Fast path (steps 1-2) on a first word (lo, hi)
 // ---------------------------------------------------------------------------
-// x = RN(U X_i) computed as fma(1 + U, X_i, -X_i): (1 + U) X_i - X_i equals
-// U X_i exactly and the FMA rounds once.  The normal's sign (bit 8) is put
-// on the result's sign bit.
+// x = RN(U sX) computed as fma(1 + U, sX, -sX): (1 + U) sX - sX equals
+// U sX exactly and the FMA rounds once.  sX is read from a table of
+// 2 i_max entries indexed by i | sign << IB: +X_i, then -X_i for the
+// normal's negative draws (the exponential reads the first half only), so
+// the sign costs nothing; a zero (U = 0) comes out +0 for either sign.
 template <int DIST, int IB = 8>
 __device__ __forceinline__ double fast_value(uint32_t lo, uint32_t hi, const double* sX) {
-  const double X = sX[lo & ((1u << IB) - 1u)];
+  constexpr uint32_t kMask = ((DIST == ZIG_NORMAL ? 2u : 1u) << IB) - 1u;
+  const double X = sX[lo & kMask];
   const double one_u = __hiloint2double((int)(0x3FF00000u | (hi >> 12)),
                                         (int)__funnelshift_r(lo, hi, 12));
-  const double x = __fma_rn(one_u, X, -X);
-  if (DIST == ZIG_EXP) return x;
-  return __hiloint2double(__double2hiint(x) ^ (int)((lo & (1u << IB)) << (31 - IB)),
-                          __double2loint(x));
+  return __fma_rn(one_u, X, -X);
 }
 
 template <int DIST, int IB = 8>
 __device__ __forceinline__ float fast_value(uint32_t lo, uint32_t hi, const float* sX) {
-  const float X = sX[lo & ((1u << IB) - 1u)];
-  const float x = __fmaf_rn(__int_as_float((int)(0x3F800000u | (hi >> 9))), X, -X);
-  if (DIST == ZIG_EXP) return x;
-  return __int_as_float(__float_as_int(x) ^ (int)((lo & (1u << IB)) << (31 - IB)));
+  constexpr uint32_t kMask = ((DIST == ZIG_NORMAL ? 2u : 1u) << IB) - 1u;
+  const float X = sX[lo & kMask];
+  return __fmaf_rn(__int_as_float((int)(0x3F800000u | (hi >> 9))), X, -X);
 }
 
 }  // namespace zig

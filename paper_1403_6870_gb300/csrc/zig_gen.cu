@@ -197,7 +197,7 @@ struct WarpQueues {
 // Shared state of one CTA (X_i of an index of IB bits).
 template <typename T, int IB = 8>
 struct CtaState {
-  T sX[1 << IB];
+  T sX[2 << IB];  // +X_i, then -X_i (the normal's negative draws)
   WarpQueues wq[kWarps];
 };
 
@@ -763,7 +763,10 @@ __global__ void __launch_bounds__(kThreads, Shp::MB)
   __shared__ unsigned shist[Sink::kReduce ? kBins : 1];
 
   const int tid = threadIdx.x;
-  for (int k = tid; k < (1 << IB); k += kThreads) sh.sX[k] = Prec<T>::X(dev_tab<IB>(DIST), k);
+  for (int k = tid; k < (2 << IB); k += kThreads) {
+    const T X = Prec<T>::X(dev_tab<IB>(DIST), k & ((1 << IB) - 1));
+    sh.sX[k] = (k >> IB) ? -X : X;
+  }
   if (Sink::kReduce)
     for (int k = tid; k < kBins; k += kThreads) shist[k] = 0u;
   if constexpr (Sink::kReduce) sink.init(shist);
@@ -775,9 +778,12 @@ __global__ void __launch_bounds__(kThreads, Shp::MB)
 
   if constexpr (Sink::kReduce) {
     // CTA partials in thread order, then the CTA's histogram into the
-    // output; the last CTA to finish sums the partials in CTA order.
-    __shared__ double rsum[kThreads][4];
+    // output; the last CTA to finish sums the partials in CTA order.  The
+    // partials reuse the warp queues, empty once every warp has drained.
+    static_assert(sizeof(sh.wq) >= kThreads * 4 * sizeof(double), "partials fit the queues");
+    double (*rsum)[4] = reinterpret_cast<double (*)[4]>(&sh.wq[0]);
     __shared__ bool last_cta;
+    __syncthreads();
     for (int k = 0; k < 4; ++k) rsum[tid][k] = sink.acc[k];
     __syncthreads();
     if (tid < 4) {
