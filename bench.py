@@ -388,6 +388,7 @@ def run_zig(args):
         line["packed_keying"] = measure_packed(z, stream)
         line["i_max_1024"] = measure_i1024(z, stream)
         line["fused"] = measure_fused(z, stream)
+        line["precision_f32"] = measure_precision(z, stream)
         del out
         torch.cuda.empty_cache()
         line["batch"] = measure_batch(z, stream)
@@ -568,6 +569,61 @@ def measure_i1024(z, stream, steps: int = 100):
     res["note"] = ("index_bits 10: i_max = 1024 tables (fast path 1020/1024 exponential, "
                    "1021/1024 normal); outputs differ from the 256-slot tables and are checked "
                    "against the oracle on its 10-bit tables")
+    return res
+
+
+def measure_precision(z, stream):
+    """The FP32 generator against FP64 on the same counters: for each
+    distribution, the 2^30 counters of the FP32 workload in both precisions.
+    The FP64 outputs are the oracle's (bit for bit on the fast path, within
+    2 ulp elsewhere: the parity tests), so these figures compare the FP32
+    outputs with the FP64 definition of the method.  A decision that flips
+    between the precisions sends the draw down another path (a new attempt
+    or the other region), far beyond the rounding gap of agreeing paths,
+    which is below 2^-23 (|x| + X_0) (U keeps 23 of its 52 bits, tables are
+    RN32 of the binary128 values); `far_fraction` counts differences above
+    4x that gap."""
+    import torch
+
+    res = {}
+    chunk = 1 << 26
+    for name, dist in (("exp", W.EXP), ("normal", W.NORMAL)):
+        c = W.WORKLOADS[f"{name}_f32_2p30"]
+        n, off = c["n"], c["offset"]
+        fn = z.zig_exponential if dist == W.EXP else z.zig_normal
+        x32 = torch.empty(n, dtype=torch.float32, device="cuda")
+        x64 = torch.empty(n, dtype=torch.float64, device="cuda")
+        fn(x32, n, W.SEED, off, stream=stream)
+        fn(x64, n, W.SEED, off, stream=stream)
+        torch.cuda.synchronize()
+        x0 = float(z.zig_export_tables(dist).X[0])
+        max_abs = max_ulp_ge1 = max_ulp_near = 0.0
+        same_rn = far = 0
+        for k in range(0, n, chunk):
+            a = x32[k:k + chunk].double()
+            b = x64[k:k + chunk]
+            d = (a - b).abs()
+            max_abs = max(max_abs, float(d.max()))
+            same_rn += int((a == b.float().double()).sum())
+            isfar = d > 2.0**-21 * (b.abs() + x0)
+            far += int(isfar.sum())
+            ulp = torch.ldexp(torch.ones_like(b), torch.frexp(b)[1] - 24)
+            r = torch.where(isfar, torch.zeros_like(d), d / ulp)
+            max_ulp_near = max(max_ulp_near, float(r.max()))
+            big = (b.abs() >= 1.0) & ~isfar
+            if bool(big.any()):
+                max_ulp_ge1 = max(max_ulp_ge1, float((d / ulp)[big].max()))
+        del x32, x64
+        res[name] = {"n": n, "max_abs_diff": max_abs,
+                     "max_ulp32_where_abs_ge_1": max_ulp_ge1,
+                     "max_ulp32_agreeing_paths": max_ulp_near,
+                     "frac_equal_to_rn32_of_fp64": same_rn / n,
+                     "far_fraction": far / n}
+    torch.cuda.empty_cache()
+    res["note"] = ("2^30 counters per distribution (the FP32 workloads), FP32 vs FP64 outputs of "
+                   "this library on the same counters; ulp32 = FP32 ulp at the FP64 value. Near "
+                   "zero the FP32 value differs from the FP64 one by up to X_i 2^-23 because U "
+                   "keeps its top 23 bits, hence large ulp ratios there")
     return res
 
 
