@@ -359,7 +359,8 @@ def run_zig(args):
         "data": "synthetic (Philox counters; seed 0x0123456789ABCDEF, fresh counters per step)",
         "config": {"workload": args.workload, "dist": "normal" if c["dist"] else "exponential",
                    "n_per_step_per_gpu": n, "output_bytes": n * esize,
-                   "l2": "output 2 GiB per step > 129 MB L2; no flush",
+                   "l2": "output {:.2f} GiB per step {} 129 MB L2; no flush".format(
+                       n * esize / 2**30, ">" if n * esize > 129e6 else "<="),
                    "parallelism": f"counter-range shards x{world}"},
         "clocks": clk.summary(),
         "gpu_launches": args.steps,
