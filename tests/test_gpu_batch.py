@@ -115,3 +115,26 @@ def test_serving_mix_sampled(zig, orc):
         idx = np.unique(np.concatenate([[0, n - 1], rng.integers(0, n, size=8)])).astype(np.uint64)
         got = b[torch.from_numpy(idx.astype(np.int64)).cuda()].cpu().numpy()
         _compare(orc, q, got, idx)
+
+
+def test_identity_parameters_equal_plain_calls(zig):
+    # rate 1 and (mean 0, sd 1) make the folded fast path RN((1 + U) sX - sX)
+    # and leave fringe draws unchanged, so each request equals the plain call
+    # on the same key and counters bit for bit
+    reqs = []
+    for k, n in enumerate([1, 7, 3584 * 5 + 3, 100003, 1 << 20]):
+        for dist in (0, 1):
+            for dtype in (0, 1):
+                reqs.append(dict(n=n, dist=dist, dtype=dtype, seed=W.splitmix64(100 + k),
+                                 offset=(k * 2**31 + 77) if k != 2 else 2**32 - 5000,
+                                 p0=1.0 if dist == 0 else 0.0, p1=0.0 if dist == 0 else 1.0))
+    bufs = _alloc(reqs, lambda r: r % 2)
+    _serve(zig, reqs)
+    for q, (b, pad) in zip(reqs, bufs):
+        got = b[pad:pad + q["n"]]
+        want = torch.empty_like(got)
+        fn = zig.zig_exponential if q["dist"] == 0 else zig.zig_normal
+        fn(want, q["n"], q["seed"], q["offset"])
+        it = torch.int64 if q["dtype"] == 1 else torch.int32
+        assert torch.equal(got.view(it), want.view(it)), q
+    assert zig.zig_status_poll() == zig.ZIG_OK

@@ -197,3 +197,21 @@ def test_f32_2p30_full_size(zig, orc, name):
         assert abs(moms[0] - 1) < 5 * math.sqrt(1 / n) and abs(moms[1] - 2) < 5 * math.sqrt(20 / n)
     else:
         assert abs(moms[0]) < 5 * math.sqrt(1 / n) and abs(moms[1] - 1) < 5 * math.sqrt(2 / n)
+
+
+def test_f32_zeros_are_positive_and_match_oracle(zig, orc):
+    # FP32 keeps 23 bits of U, so U = 0 comes up about once in 2^23 draws:
+    # every such fast-path value is +0 whatever the normal's sign (reading
+    # R16), on the GPU as in the oracle.
+    n = 1 << 27
+    for dist in (W.NORMAL, W.EXP):
+        out, _ = gpu_gen(zig, dist, W.F32, n, W.SEED, 12345)
+        bits = out.view(torch.int32)
+        zpos = torch.nonzero((bits & 0x7FFFFFFF) == 0).flatten()
+        assert zpos.numel() >= 4  # ~16 expected
+        assert int((bits[zpos] != 0).sum()) == 0
+        idx = zpos.cpu().numpy().astype(np.uint64)
+        ref, words, margin = oracle_ref(orc, dist, W.F32, W.SEED, 12345, idx=idx)
+        assert np.array_equal(ref.astype(np.float32).view(np.uint32),
+                              out[zpos].cpu().numpy().view(np.uint32))
+    assert zig.zig_status_poll() == zig.ZIG_OK
