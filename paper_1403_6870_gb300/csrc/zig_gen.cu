@@ -237,15 +237,17 @@ __device__ __forceinline__ int hist_bin(double x) {
 }
 
 // MomentSink: the values are never stored; each thread accumulates x, x^2,
-// x^3, x^4 (FP32 values in FP32 over one tile, then added to FP64
-// accumulators; FP64 values in FP64) and counts the value in the CTA's
-// shared-memory histogram.  Outputs still to be patched are skipped here and
+// x^3, x^4 (FP32 values in FP32 over one tile, then added to a double-FP32
+// accumulator (hi, lo) by an error-free two-sum, which keeps GB300's slow
+// FP64 pipe out of the loop; FP64 values in FP64) and counts the value in
+// the CTA's shared-memory histogram.  Outputs still to be patched are skipped here and
 // counted when the fringe stages put their final value.
 template <typename T>
 struct MomentSink {
   unsigned* hist;  // CTA shared histogram, kBins entries
-  double acc[4];
+  double acc[4];   // FP64 values: the sums; FP32 values: set by finish()
   T part[4];
+  float hi[4], lo[4];  // FP32 values: double-FP32 sums of the tile partials
   static constexpr bool kReduce = true;
   static constexpr bool kAffine = false;
   __device__ __forceinline__ void init(unsigned* h) {
@@ -253,6 +255,7 @@ struct MomentSink {
     for (int k = 0; k < 4; ++k) {
       acc[k] = 0.0;
       part[k] = (T)0;
+      hi[k] = lo[k] = 0.0f;
     }
   }
   __device__ __forceinline__ void add(T x) {
@@ -273,8 +276,24 @@ struct MomentSink {
   __device__ __forceinline__ void tile_end() {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      acc[k] = __dadd_rn(acc[k], (double)part[k]);
+      if constexpr (sizeof(T) == 8) {
+        acc[k] = __dadd_rn(acc[k], (double)part[k]);
+      } else {
+        // two-sum (Knuth): s + e == hi + part exactly
+        const float s = __fadd_rn(hi[k], (float)part[k]);
+        const float b = __fsub_rn(s, hi[k]);
+        const float e = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, b)), __fsub_rn((float)part[k], b));
+        hi[k] = s;
+        lo[k] = __fadd_rn(lo[k], e);
+      }
       part[k] = (T)0;
+    }
+  }
+  // the thread's sums in FP64 (after its last tile)
+  __device__ __forceinline__ void finish() {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] = __dadd_rn((double)hi[k], (double)lo[k]);
     }
   }
   __device__ __forceinline__ void put(uint64_t, T x) {
@@ -783,6 +802,7 @@ __global__ void __launch_bounds__(kThreads, Shp::MB)
     static_assert(sizeof(sh.wq) >= kThreads * 4 * sizeof(double), "partials fit the queues");
     double (*rsum)[4] = reinterpret_cast<double (*)[4]>(&sh.wq[0]);
     __shared__ bool last_cta;
+    sink.finish();
     __syncthreads();
     for (int k = 0; k < 4; ++k) rsum[tid][k] = sink.acc[k];
     __syncthreads();

@@ -5,7 +5,8 @@ The variates are those of zig_normal/zig_exponential on the same counters
 apply: the histogram must equal the oracle's exactly; each power sum must
 be within the rounding bound of its accumulation scheme (FP32 partials of
 at most m terms, m = 32 at the default FP32 shape and 64 with packed
-keying, plus FP64 accumulation):
+keying, then summed in double-FP32 by an error-free two-sum, whose error is
+far below the bound):
 |S_gpu - S| <= (m + 4) 2^-24 sum |x|^k (FP32) or 1e-12 sum |x|^k (FP64).
 Packed keying (zig_moments_keyed) is checked against the oracle's packed
 word source the same way.
