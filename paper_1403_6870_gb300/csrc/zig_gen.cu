@@ -244,7 +244,7 @@ __device__ __forceinline__ int hist_bin(double x) {
 // counted when the fringe stages put their final value.
 template <typename T>
 struct MomentSink {
-  unsigned* hist;  // CTA shared histogram, kBins entries
+  unsigned* hist;  // CTA shared histogram, kBins entries and one unused slot
   double acc[4];   // FP64 values: the sums; FP32 values: set by finish()
   T part[4];
   float hi[4], lo[4];  // FP32 values: double-FP32 sums of the tile partials
@@ -258,20 +258,28 @@ struct MomentSink {
       hi[k] = lo[k] = 0.0f;
     }
   }
-  __device__ __forceinline__ void add(T x) {
+  __device__ __forceinline__ void add_powers(T x) {
     typedef Prec<T> P;
     const T x2 = P::mul(x, x);
     part[0] = P::add(part[0], x);
     part[1] = P::add(part[1], x2);
     part[2] = P::fmat(x2, x, part[2]);
     part[3] = P::fmat(x2, x2, part[3]);
+  }
+  __device__ __forceinline__ void add(T x) {
+    add_powers(x);
     atomicAdd(&hist[hist_bin(x)], 1u);
   }
+  // Without branches: an output still to be patched adds zero to the power
+  // sums and counts in the unused slot kBins.
   template <int V>
   __device__ __forceinline__ void vec(uint64_t, const T* v, unsigned fringe) {
 #pragma unroll
-    for (int k = 0; k < V; ++k)
-      if (!((fringe >> k) & 1u)) add(v[k]);
+    for (int k = 0; k < V; ++k) {
+      const bool patch = (fringe >> k) & 1u;
+      add_powers(patch ? (T)0 : v[k]);
+      atomicAdd(&hist[patch ? kBins : hist_bin(v[k])], 1u);
+    }
   }
   __device__ __forceinline__ void tile_end() {
 #pragma unroll
@@ -779,7 +787,7 @@ __global__ void __launch_bounds__(kThreads, Shp::MB)
   constexpr int R = Shp::R;
   constexpr int kTile = kPThreads * R;
   __shared__ CtaState<T, IB> sh;
-  __shared__ unsigned shist[Sink::kReduce ? kBins : 1];
+  __shared__ unsigned shist[Sink::kReduce ? kBins + 1 : 1];
 
   const int tid = threadIdx.x;
   for (int k = tid; k < (2 << IB); k += kThreads) {
