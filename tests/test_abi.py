@@ -173,3 +173,49 @@ def test_wide_tables_equal_oracle_tables(zig, orc, dist, bits):
     assert list(t.alias)[:M] == list(r.alias)[:M]
     with pytest.raises(zig.ZigError):
         zig.zig_export_tables_ex(dist, 9)
+
+
+def test_generate_argument_checks(zig):
+    call = zig.raw_call
+    Z = zig
+    KI, KP = Z.ZIG_KEY_INDEX, Z.ZIG_KEY_PACKED
+    # keying, index width and the packed FP32 word that has no room for 10 index bits
+    assert call("zig_generate", 1, 2, 8, 0x1000, 10, 1, 0, Z.ZIG_F64, None) == Z.ZIG_E_INVAL
+    assert call("zig_generate", 1, KI, 9, 0x1000, 10, 1, 0, Z.ZIG_F64, None) == Z.ZIG_E_INVAL
+    assert call("zig_generate", 1, KP, 10, 0x1000, 10, 1, 0, Z.ZIG_F32, None) == Z.ZIG_E_INVAL
+    assert call("zig_generate", 2, KI, 8, 0x1000, 10, 1, 0, Z.ZIG_F64, None) == Z.ZIG_E_INVAL
+    # the same size, alignment and range rules as the plain calls
+    assert call("zig_generate", 0, KP, 8, None, 0, 1, 0, Z.ZIG_F32, None) == Z.ZIG_OK
+    assert call("zig_generate", 0, KP, 8, None, 4, 1, 0, Z.ZIG_F32, None) == Z.ZIG_E_INVAL
+    assert call("zig_generate", 0, KI, 10, 0x1004, 4, 1, 0, Z.ZIG_F64, None) == Z.ZIG_E_ALIGN
+    assert call("zig_generate", 1, KP, 10, 0x1000, 3, 1, 2**64 - 2, Z.ZIG_F64,
+                None) == Z.ZIG_E_RANGE
+
+
+def test_batch_validate_rules(zig):
+    import numpy as np
+
+    Z = zig
+    good = dict(out=0x10000, n=1000, seed=1, offset=5, dist=1, dtype=1, p0=-2.0, p1=0.5)
+
+    def status(**change):
+        q = dict(good)
+        q.update(change)
+        return Z.zig_batch_validate(Z.pack_requests([good, q]))
+
+    assert status() == Z.ZIG_OK
+    assert status(dist=0, p0=0.3, p1=0.0) == Z.ZIG_OK
+    assert status(dist=2) == Z.ZIG_E_INVAL
+    assert status(dtype=3) == Z.ZIG_E_INVAL
+    assert status(out=0) == Z.ZIG_E_INVAL
+    assert status(out=0, n=0) == Z.ZIG_OK          # an empty request needs no buffer
+    assert status(out=0x10004) == Z.ZIG_E_ALIGN     # FP64 needs 8-byte alignment
+    assert status(out=0x10004, dtype=0) == Z.ZIG_OK  # FP32 needs 4
+    assert status(n=2**40) == Z.ZIG_E_RANGE
+    assert status(offset=2**64 - 999) == Z.ZIG_E_RANGE
+    assert status(offset=2**64 - 1000) == Z.ZIG_OK  # the last counter is 2^64 - 1
+    for bad in (0.0, -1.0, float("inf"), float("nan")):
+        assert status(dist=0, p0=bad) == Z.ZIG_E_INVAL  # exponential rate
+        assert status(p1=bad) == Z.ZIG_E_INVAL          # normal standard deviation
+    assert status(p0=float("nan")) == Z.ZIG_E_INVAL     # normal mean
+    assert Z.zig_batch_validate(np.zeros(0, dtype=Z.request_dtype())) == Z.ZIG_OK
