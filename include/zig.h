@@ -255,7 +255,11 @@ zig_status zig_moments_keyed(zig_dist dist, zig_dtype dtype, int keying, uint64_
  * device array of 64 KiB in the library, present on every device that
  * loads the library until the process exits; its device address is taken
  * by zig_build_tables, which must have run on the current device (as for
- * every entry point).  All calls share that array and it keeps the last
+ * every entry point).  zig_build_tables also launches each of this entry
+ * point's kernels once on an empty range, so that the driver loads their
+ * code and sizes their local memory then, not during a later call here
+ * (under lazy module loading either could otherwise take device memory on
+ * the first call).  All calls share that array and it keeps the last
  * call's contents; each call clears the part that must start at zero.
  * Calls whose executions overlap on the GPU (any device-side concurrency,
  * e.g. two streams) race on the array and give wrong results: serialise
@@ -270,14 +274,29 @@ zig_status zig_moments_noalloc(zig_dist dist, zig_dtype dtype, uint64_t n,
 /*
  * Batched requests: many generation calls served by one persistent launch.
  * Each request asks for n variates of its own distribution and precision,
- * under its own Philox key and counter offset (element t of request r is
- * the variate of counter offset_r + t, exactly as zig_exponential /
- * zig_normal would write it before the transform), then transformed:
- *   exponential with rate lambda = p0 > 0:   x * RN(1 / lambda);
- *   normal with mean mu = p0, sd sigma = p1 > 0:  fma(sigma, z, mu);
- * FP32 requests use RN32(RN64(1/lambda)), RN32(mu), RN32(sigma) and binary32
- * arithmetic.  The paper's method has no batched interface; the transforms
- * are the standard scale and location changes of Exp(1) and N(0, 1).
+ * under its own Philox key and counter offset.  Element t of request r is
+ * defined from the standard variate z of counter offset_r + t (exactly what
+ * zig_exponential / zig_normal write there) by the standard scale and
+ * location change of Exp(1) and N(0, 1):
+ *   exponential with rate lambda = p0 > 0:        y = RN(z * RN(1/lambda));
+ *   normal with mean mu = p0, sd sigma = p1 > 0:  y = RN(sigma z + mu) (one fma);
+ * FP32 requests use s = RN32(RN64(1/lambda)), RN32(mu), RN32(sigma) and
+ * binary32 arithmetic.  The paper's method has no batched interface.
+ *
+ * What the library returns: exactly y for every draw that leaves step 2 of
+ * Table 1 (overhang and tail draws).  For a step-2 draw (z = +-RN(U X_i))
+ * the map is folded into the step's single rounding, which saves one
+ * floating-point operation per value:
+ *   y' = RN((1 + U)(+-B_i) + D),  B_i = RN(s X_i),  D = RN(m -+ B_i)
+ * (s = RN(1/lambda), m = 0 for the exponential; s = sigma, m = mu for the
+ * normal; signs those of the normal's sign bit).  With unit roundoff u
+ * (2^-53 for FP64, 2^-24 for FP32) it satisfies
+ *   exponential:  |y' - y| <= 4u|y|                       (a few ulp of y);
+ *   normal:       |y' - y| <= 4u|y| + 2u|mu| + u|mu -+ sigma X_i|,
+ * up to second-order terms: both y and y' are within a few units of
+ * roundoff of the exact mu +- sigma U X_i, so where mu cancels sigma z the
+ * bound is absolute (in units of |mu|), as for any rounded evaluation of
+ * the map.  With rate 1, or mean 0 and sd 1, y' = y bit for bit.
  */
 typedef struct zig_request {
   void* out;       /* device array of n float (ZIG_F32) or double elements */
@@ -316,7 +335,10 @@ zig_status zig_batch(const zig_request* d_reqs, uint32_t count,
 
 /*
  * zig_status_poll -- read and clear this device's status word.
- * Synchronises stream first.  Returns ZIG_OK if no device-side condition
+ * The read-and-clear is one atomic exchange ordered on stream (after the
+ * work queued there), and the call then synchronises that stream only, not
+ * the device: a bit set meanwhile by work on another stream is kept for
+ * the next poll.  Returns ZIG_OK if no device-side condition
  * was recorded since the last poll, ZIG_E_LOOP_LIMIT if a fringe loop hit
  * its cap (those outputs are NaN), ZIG_E_INVAL if zig_batch skipped an
  * invalid request, ZIG_E_NOTINIT or ZIG_E_CUDA.  ZIG_E_TIMEOUT is

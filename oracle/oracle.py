@@ -147,12 +147,9 @@ def lib():
                                              ctypes.c_double, ctypes.c_void_p, ctypes.c_uint64,
                                              ctypes.c_void_p, ctypes.c_int]
             L.orc_request_values.restype = ctypes.c_int64
-            L.orc_request_fast64.argtypes = [ctypes.c_int, ctypes.c_uint64, P(Tables),
-                                             ctypes.c_double, ctypes.c_double]
-            L.orc_request_fast64.restype = ctypes.c_double
-            L.orc_request_fast32.argtypes = [ctypes.c_int, ctypes.c_uint64, P(Tables),
-                                             ctypes.c_double, ctypes.c_double]
-            L.orc_request_fast32.restype = ctypes.c_float
+            L.orc_first_words.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                          ctypes.c_uint64, ctypes.c_void_p]
+            L.orc_first_words.restype = None
         return _lib
 
 
@@ -279,23 +276,29 @@ def enum_overhang(t: Tables, j: int, bits: int) -> np.ndarray:
 
 
 def request_values(req: dict, idx) -> np.ndarray:
-    """Transformed variates of one batched request at positions idx (float64;
-    FP32 results widened exactly)."""
+    """Variates of one batched request at positions idx: the standard variate
+    of each counter mapped by transform() (float64; FP32 results widened
+    exactly)."""
     idx = np.ascontiguousarray(idx, dtype=np.uint64)
     out = np.empty(idx.size, dtype=np.float64)
     te, tn = tables(EXP), tables(NORMAL)
-    lib().orc_request_values(ctypes.byref(te), ctypes.byref(tn), req["dist"], req["dtype"],
-                             req["seed"] & (2**64 - 1), req["offset"] & (2**64 - 1),
-                             float(req["p0"]), float(req["p1"]), idx.ctypes.data, idx.size,
-                             out.ctypes.data, default_threads())
+    rc = lib().orc_request_values(ctypes.byref(te), ctypes.byref(tn), req["dist"],
+                                  req["dtype"], req["seed"] & (2**64 - 1),
+                                  req["offset"] & (2**64 - 1), float(req["p0"]),
+                                  float(req["p1"]), idx.ctypes.data, idx.size, out.ctypes.data,
+                                  default_threads())
+    if rc < 0:
+        raise MemoryError("orc_request_values could not allocate its scratch")
     return out
 
 
-def request_fast(dist: int, dtype: int, w0: int, p0: float, p1: float) -> float:
-    """A request's fast-path value from its first word (orc_request_fast64/32)."""
-    t = tables(dist)
-    fn = lib().orc_request_fast64 if dtype == F64 else lib().orc_request_fast32
-    return float(fn(dist, w0 & (2**64 - 1), ctypes.byref(t), float(p0), float(p1)))
+def first_words(seed: int, offset: int, idx) -> np.ndarray:
+    """First word (block 0, r0 | r1 << 32) of counters offset + idx."""
+    idx = np.ascontiguousarray(idx, dtype=np.uint64)
+    out = np.empty(idx.size, dtype=np.uint64)
+    lib().orc_first_words(seed & (2**64 - 1), offset & (2**64 - 1), idx.ctypes.data, idx.size,
+                          out.ctypes.data)
+    return out
 
 
 def transform(dist: int, dtype: int, x: float, p0: float, p1: float) -> float:

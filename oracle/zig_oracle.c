@@ -822,50 +822,29 @@ float orc_transform32(int dist, float x, double p0, double p1) {
   return fmaf((float)p1, x, (float)p0);
 }
 
-double orc_request_fast64(int dist, uint64_t w0, const orc_tables* t, double p0, double p1) {
-  const int i = (int)(w0 & (uint64_t)(t->imax - 1));
-  const int neg = dist == ORC_NORMAL && ((w0 >> t->ibits) & 1u);
-  const double s = dist == ORC_EXP ? 1.0 / p0 : p1;
-  const double mm = dist == ORC_EXP ? 0.0 : p0;
-  const double B = s * t->X[i];
-  const double D = neg ? mm + B : mm - B;
-  const double one_u = 1.0 + ldexp((double)(w0 >> 12), -52); /* exact */
-  return fma(one_u, neg ? -B : B, D);
-}
-
-float orc_request_fast32(int dist, uint64_t w0, const orc_tables* t, double p0, double p1) {
-  const int i = (int)(w0 & (uint64_t)(t->imax - 1));
-  const int neg = dist == ORC_NORMAL && ((w0 >> t->ibits) & 1u);
-  const float s = dist == ORC_EXP ? (float)(1.0 / p0) : (float)p1;
-  const float mm = dist == ORC_EXP ? 0.0f : (float)p0;
-  const float B = s * t->X32[i];
-  const float D = neg ? mm + B : mm - B;
-  const float one_u = 1.0f + ldexpf((float)(w0 >> 41), -23); /* exact */
-  return fmaf(one_u, neg ? -B : B, D);
-}
-
 int64_t orc_request_values(const orc_tables* te, const orc_tables* tn, int dist, int dtype,
                            uint64_t seed, uint64_t offset, double p0, double p1,
                            const uint64_t* idx, uint64_t m, double* out, int nthreads) {
+  /* the standard variate of each counter, then the request's map */
   int64_t errs;
-  const orc_tables* t = dist == ORC_EXP ? te : tn;
   if (dtype == ORC_F64) {
     errs = orc_fill(te, tn, dist, dtype, seed, offset, m, idx, out, NULL, NULL, nthreads);
     for (uint64_t k = 0; k < m; k++) out[k] = orc_transform64(dist, out[k], p0, p1);
   } else {
-    float* tmp = (float*)malloc(m * sizeof(float));
+    float* tmp = (float*)malloc((m ? m : 1) * sizeof(float));
+    if (tmp == NULL) return -1;
     errs = orc_fill(te, tn, dist, dtype, seed, offset, m, idx, tmp, NULL, NULL, nthreads);
     for (uint64_t k = 0; k < m; k++) out[k] = (double)orc_transform32(dist, tmp[k], p0, p1);
     free(tmp);
   }
-  /* fast-path draws: the affine map folded into the one rounding */
+  return errs;
+}
+
+void orc_first_words(uint64_t seed, uint64_t offset, const uint64_t* idx, uint64_t m,
+                     uint64_t* out) {
   for (uint64_t k = 0; k < m; k++) {
     orc_words w;
     orc_words_philox(&w, seed, offset + (idx ? idx[k] : k));
-    const uint64_t w0 = orc_next(&w);
-    if ((int)(w0 & (uint64_t)(t->imax - 1)) < t->L)
-      out[k] = dtype == ORC_F64 ? orc_request_fast64(dist, w0, t, p0, p1)
-                                : (double)orc_request_fast32(dist, w0, t, p0, p1);
+    out[k] = orc_next(&w);
   }
-  return errs;
 }

@@ -202,24 +202,20 @@ int64_t orc_enum_overhang(const orc_tables* t, int j, int bits, double* xs);
 double orc_transform64(int dist, double x, double p0, double p1);
 float orc_transform32(int dist, float x, double p0, double p1);
 
-/* A request's variate when step 2 of Table 1 returns it (layer index i of
- * the first word w0 below L_max): the affine map is folded into the one
- * rounding of the fast path.  With scale s and shift m (exponential:
- * s = RN(1/lambda), m = 0; normal: s = sigma, m = mu), B_i = RN(s X_i) and,
- * for the draw's sign, D = RN(m - B_i) (positive) or RN(m + B_i)
- * (negative), the value is RN((1 + U)(+-B_i) + D), i.e. m + s U X_i up to
- * the roundings of B_i and D.  FP32 requests do the same in binary32 with
- * RN32 of the FP64 s and m and the binary32 tables.  Other draws get
- * orc_transform64/32 of their variate. */
-double orc_request_fast64(int dist, uint64_t w0, const orc_tables* t, double p0, double p1);
-float orc_request_fast32(int dist, uint64_t w0, const orc_tables* t, double p0, double p1);
-
 /* out[k] = variate idx[k] of a request (dist, dtype, seed, offset, p0, p1):
- * orc_request_fast64/32 for fast-path draws, else the transformed variate;
- * values as double (FP32 results widened exactly). */
+ * the standard variate of counter offset + idx[k] (orc_fill) mapped by
+ * orc_transform64/32, for every draw; values as double (FP32 results
+ * widened exactly).  Returns the number of draws that hit a loop cap, or
+ * -1 if scratch memory could not be allocated. */
 int64_t orc_request_values(const orc_tables* te, const orc_tables* tn, int dist, int dtype,
                            uint64_t seed, uint64_t offset, double p0, double p1,
                            const uint64_t* idx, uint64_t m, double* out, int nthreads);
+
+/* out[k] = the first word of counter offset + idx[k] under key seed (block
+ * 0, words r0 | r1 << 32 of C-1): the word that carries the layer index, the
+ * normal's sign and U_1. */
+void orc_first_words(uint64_t seed, uint64_t offset, const uint64_t* idx, uint64_t m,
+                     uint64_t* out);
 
 size_t orc_tables_size(void);
 

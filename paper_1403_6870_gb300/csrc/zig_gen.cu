@@ -1037,6 +1037,12 @@ uint64_t moment_grid_cap(int dev) {
 
 constexpr size_t kTicketBytes = 256;  // workspace: ticket, then the partials
 
+// zig_status_poll's read-and-clear of the status word, ordered on the
+// caller's stream: one atomic exchange, so that a bit set by a kernel on
+// another stream in between is kept for the next poll.
+__device__ unsigned int g_status_taken;
+__global__ void status_take_kernel() { g_status_taken = atomicExch(&g_status, 0u); }
+
 template <int DIST, typename T, typename Shp = GenShape<T>, int KEY = 0>
 zig_status launch_moments(uint64_t n, uint64_t seed, uint64_t offset, double* d_sums,
                           unsigned long long* d_hist, void* d_ws, size_t ws_bytes,
@@ -1226,6 +1232,27 @@ int variant_occupancy_any(int dist, int dtype, int k, int dev) {
                           : variant_occupancy<ZIG_NORMAL, float>(k, dev);
 }
 
+// One empty launch of each fused-reduction kernel zig_moments_noalloc can
+// run, on the static scratch (ticket and one CTA's partials at 0, sums at
+// 1 KiB, the histogram at 2 KiB), so that the driver loads their code and
+// sizes their local memory here, inside zig_build_tables, rather than on a
+// later zig_moments_noalloc call (either can take device memory).
+zig_status preload_moment_kernels(int dev) {
+  static_assert(2048 + kBins * sizeof(unsigned long long) <= kStaticScratchBytes,
+                "preload outputs fit the static scratch");
+  char* base = (char*)g_dev[dev].d_static_scratch;
+  double* sums = (double*)(base + 1024);
+  unsigned long long* hist = (unsigned long long*)(base + 2048);
+  const size_t ws = 1024;
+  zig_status st = launch_moments<ZIG_EXP, float>(0, 0, 0, sums, hist, base, ws, 0, dev);
+  if (st == ZIG_OK) st = launch_moments<ZIG_EXP, double>(0, 0, 0, sums, hist, base, ws, 0, dev);
+  if (st == ZIG_OK) st = launch_moments<ZIG_NORMAL, float>(0, 0, 0, sums, hist, base, ws, 0, dev);
+  if (st == ZIG_OK) st = launch_moments<ZIG_NORMAL, double>(0, 0, 0, sums, hist, base, ws, 0, dev);
+  if (st == ZIG_OK && cudaStreamSynchronize(0) != cudaSuccess) st = ZIG_E_CUDA;
+  if (st != ZIG_OK) cudaGetLastError();
+  return st;
+}
+
 }  // namespace
 
 const zig_tables_export* host_tables(int dist) {
@@ -1299,6 +1326,8 @@ zig_status zig_build_tables(void) {
   g_dev[dev].d_static_scratch = scratch;
   g_dev[dev].sms = sms;
   std::snprintf(g_dev[dev].name, sizeof(g_dev[dev].name), "%s", prop.name);
+  st = preload_moment_kernels(dev);
+  if (st != ZIG_OK) return st;
   static std::once_flag env_cache;
   std::call_once(env_cache, [] {
     const char* path = std::getenv("ZIG_TUNE_CACHE");
@@ -1573,11 +1602,13 @@ zig_status zig_status_poll(void* stream) {
   zig_status st = current_device(&dev);
   if (st != ZIG_OK) return st;
   if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
+  cudaStream_t s = (cudaStream_t)stream;
   unsigned int h = 0;
-  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
-      cudaMemcpy(&h, g_dev[dev].d_status, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemset(g_dev[dev].d_status, 0, sizeof(h)) != cudaSuccess ||
-      cudaDeviceSynchronize() != cudaSuccess) {
+  status_take_kernel<<<1, 1, 0, s>>>();
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyFromSymbolAsync(&h, g_status_taken, sizeof(h), 0, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return ZIG_E_CUDA;
   }
