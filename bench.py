@@ -38,7 +38,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gen_kernel_normal_f64_traffic.txt
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=4000)
+    p.add_argument("--steps", type=int, default=500)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="zig", choices=["zig", "reference"])
     p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
@@ -156,14 +156,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rate(dist: int, dtype: int, offset: int, n: int):
-    """Oracle throughput (samples/s) on all host cores for n counters."""
+CLOCK_SOAK_S = 1.0  # the sampler's window before the timed region
+
+
+def soak(step, first: int, ms_per_step: float, stream):
+    """Untimed steps for about CLOCK_SOAK_S seconds, run just before the
+    timed region with the clock sampler already running, so that it sees
+    the same launches under load even when K steps last only milliseconds.
+    Returns the number of steps run (their counters follow `first`)."""
+    import torch
+
+    count = max(1, int(CLOCK_SOAK_S * 1e3 / max(ms_per_step, 1e-3)))
+    for k in range(count):
+        step(first + k)
+    torch.cuda.synchronize()
+    return count
+
+
+def oracle_rate(dist: int, dtype: int, offset: int, n: int, nthreads=None):
+    """Oracle throughput (samples/s) on nthreads host cores (default: all)
+    for n counters."""
     from oracle import oracle
 
     oracle.build()
     oracle.tables(oracle.EXP)
     oracle.tables(oracle.NORMAL)  # built before the timed region
-    threads = oracle.default_threads()
+    threads = nthreads or oracle.default_threads()
     t0 = time.perf_counter()
     oracle.fill(dist, dtype, W.SEED, offset, n, nthreads=threads)
     return n / (time.perf_counter() - t0), threads
@@ -233,17 +251,22 @@ def run_fused(args):
         fused_call(z, c["dist"], c["dtype"], keying, n, W.SEED,
                    step_counter(c["offset"], k, rank, world, n), sums, hist, ws, stream)
 
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     for k in range(args.warmup):
         step(k)
+    e1.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    est_ms = e0.elapsed_time(e1) / max(1, args.warmup)
     with ClockSampler(local_rank) as clk:
+        nsoak = soak(step, args.warmup, est_ms, stream)
+        first = args.warmup + nsoak
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         for k in range(args.steps):
-            step(args.warmup + k)
+            step(first + k)
         e1.record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -260,10 +283,10 @@ def run_fused(args):
     hs = torch.empty(4, dtype=torch.float64, pin_memory=True)
     hh = torch.empty(4098, dtype=torch.int64, pin_memory=True)
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(3, min(20, args.steps))
+    e2e_steps = args.steps
     f0.record(stream)
     for k in range(e2e_steps):
-        step(args.warmup + args.steps + k)
+        step(first + args.steps + k)
         hs.copy_(sums, non_blocking=True)
         hh.copy_(hist, non_blocking=True)
     f1.record(stream)
@@ -277,7 +300,8 @@ def run_fused(args):
         "config": {"workload": args.workload, "dist": "normal", "n_per_step_per_gpu": n,
                    "keying": args.keying, "l2": "nothing is stored; no flush needed",
                    "parallelism": f"counter-range shards x{world}"},
-        "clocks": clk.summary(),
+        "clocks": dict(clk.summary(), window=f"{nsoak} untimed steps of the same launch "
+                       f"(~{CLOCK_SOAK_S:.0f} s) just before the timed region, and the region"),
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": None,
@@ -326,17 +350,25 @@ def run_zig(args):
         # pick the launch shape on the workload's own output buffer (> L2)
         chosen, results = z.zig_autotune(c["dist"], c["dtype"], out, reps=3, stream=stream)
         tuned = {"chosen": chosen, "measured": results}
-    for k in range(args.warmup):
+    def step(k):
         fn(out, n, W.SEED, counter(k), stream=stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.warmup):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    est_ms = e0.elapsed_time(e1) / max(1, args.warmup)
     with ClockSampler(local_rank) as clk:
+        nsoak = soak(step, args.warmup, est_ms, stream)
+        first = args.warmup + nsoak
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         for k in range(args.steps):
-            fn(out, n, W.SEED, counter(args.warmup + k), stream=stream)
+            step(first + k)
         e1.record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -362,7 +394,8 @@ def run_zig(args):
                    "l2": "output {:.2f} GiB per step {} 129 MB L2; no flush".format(
                        n * esize / 2**30, ">" if n * esize > 129e6 else "<="),
                    "parallelism": f"counter-range shards x{world}"},
-        "clocks": clk.summary(),
+        "clocks": dict(clk.summary(), window=f"{nsoak} untimed steps of the same launch "
+                       f"(~{CLOCK_SOAK_S:.0f} s) just before the timed region, and the region"),
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
@@ -408,7 +441,7 @@ def measure_e2e(z, fn, out, n, esize, counter, stream, args):
     import torch
 
     host = torch.empty(n, dtype=out.dtype, pin_memory=True)
-    steps = max(3, min(20, args.steps // 100))
+    steps = args.steps  # as many steps as the device-timed region
 
     def timed(body):
         for k in range(2):
@@ -441,10 +474,13 @@ def measure_e2e(z, fn, out, n, esize, counter, stream, args):
 
 
 def cpu_baseline(c):
-    n = 1 << 25
+    n, n1 = 1 << 25, 1 << 22
     rate, threads = oracle_rate(c["dist"], c["dtype"], c["offset"], n)
+    rate1, _ = oracle_rate(c["dist"], c["dtype"], c["offset"], n1, nthreads=1)
     return {"value": rate / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {n} counters of the workload, all host cores"}
+            "sample": f"first {n} counters of the workload, all host cores",
+            "single_thread": {"value": rate1 / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": f"first {n1} counters of the workload, one thread"}}
 
 
 def measure_variants(z, stream, steps: int = 100):
@@ -573,19 +609,34 @@ def measure_i1024(z, stream, steps: int = 100):
     return res
 
 
-def measure_precision(z, stream):
-    """The FP32 generator against FP64 on the same counters: for each
-    distribution, the 2^30 counters of the FP32 workload in both precisions.
-    The FP64 outputs are the oracle's (bit for bit on the fast path, within
-    2 ulp elsewhere: the parity tests), so these figures compare the FP32
-    outputs with the FP64 definition of the method.  A decision that flips
-    between the precisions sends the draw down another path (a new attempt
-    or the other region), far beyond the rounding gap of agreeing paths,
-    which is below 2^-23 (|x| + X_0) (U keeps 23 of its 52 bits, tables are
-    RN32 of the binary128 values); `far_fraction` counts differences above
-    4x that gap."""
-    import torch
+def stratified_positions(n: int, m: int, rng_seed: int = 1403):
+    """m positions in [0, n), one uniform pick in each of m equal strata."""
+    import numpy as np
 
+    rng = np.random.default_rng(rng_seed)
+    width = n // m
+    return (np.arange(m, dtype=np.uint64) * np.uint64(width)
+            + rng.integers(0, width, size=m).astype(np.uint64))
+
+
+def measure_precision(z, stream, m: int = 1 << 26):
+    """The FP32 generator against the FP64 definition of the method, for the
+    2^30 counters of each FP32 workload.
+
+    Over the whole range the device's FP32 outputs are compared with its
+    FP64 outputs of the same counters (which equal the oracle's: parity
+    tests).  On a stratified subset of m counters (one uniform pick in each
+    of m equal strata) the oracle itself runs both precisions with its word
+    counts: a counter whose FP32 and FP64 draws consume different numbers
+    of words took an accept/reject decision the other way (a flip); the
+    flipped-decision rate is their share, counted by the oracle.  On the
+    same subset the device's FP32 outputs are checked against the oracle's
+    FP32 ones and measured in FP32 ulps against its FP64 ones."""
+    import numpy as np
+    import torch
+    from oracle import oracle
+
+    oracle.build()
     res = {}
     chunk = 1 << 26
     for name, dist in (("exp", W.EXP), ("normal", W.NORMAL)):
@@ -614,17 +665,38 @@ def measure_precision(z, stream):
             big = (b.abs() >= 1.0) & ~isfar
             if bool(big.any()):
                 max_ulp_ge1 = max(max_ulp_ge1, float((d / ulp)[big].max()))
+        idx = stratified_positions(n, m)
+        g32 = x32[torch.from_numpy(idx.astype(np.int64)).cuda()].cpu().numpy()
         del x32, x64
-        res[name] = {"n": n, "max_abs_diff": max_abs,
-                     "max_ulp32_where_abs_ge_1": max_ulp_ge1,
-                     "max_ulp32_agreeing_paths": max_ulp_near,
-                     "frac_equal_to_rn32_of_fp64": same_rn / n,
-                     "far_fraction": far / n}
+        r32, e32, w32, _ = oracle.fill(dist, W.F32, W.SEED, off, 0, idx=idx, want_words=True)
+        r64, e64, w64, _ = oracle.fill(dist, W.F64, W.SEED, off, 0, idx=idx, want_words=True)
+        agree = w32 == w64
+        flips = int((~agree).sum())
+        d = np.abs(g32.astype(np.float64) - r64)
+        ulp = np.ldexp(1.0, np.frexp(r64)[1] - 24)
+        ratio = np.where(agree, d / ulp, 0.0)
+        ge1 = agree & (np.abs(r64) >= 1.0)
+        res[name] = {
+            "n": n, "device_full_range": {
+                "max_abs_diff": max_abs, "max_ulp32_where_abs_ge_1": max_ulp_ge1,
+                "max_ulp32_agreeing_paths": max_ulp_near,
+                "frac_equal_to_rn32_of_fp64": same_rn / n,
+                "far_fraction": far / n,
+                "far_rule": "|x32 - x64| > 2^-21 (|x64| + X_0): a path change"},
+            "oracle_subset": {
+                "m": int(idx.size),
+                "flipped_decisions": flips, "flipped_decision_rate": flips / idx.size,
+                "max_ulp32_vs_fp64_agreeing_paths": float(ratio.max()),
+                "max_ulp32_vs_fp64_where_abs_ge_1": float(ratio[ge1].max()) if ge1.any() else 0.0,
+                "device_fp32_not_equal_oracle_fp32": int(
+                    (g32.view(np.uint32) != r32.view(np.uint32)).sum()),
+                "oracle_loop_cap_hits": e32 + e64}}
     torch.cuda.empty_cache()
-    res["note"] = ("2^30 counters per distribution (the FP32 workloads), FP32 vs FP64 outputs of "
-                   "this library on the same counters; ulp32 = FP32 ulp at the FP64 value. Near "
-                   "zero the FP32 value differs from the FP64 one by up to X_i 2^-23 because U "
-                   "keeps its top 23 bits, hence large ulp ratios there")
+    res["note"] = (f"flipped_decision_rate: the oracle's FP32 and FP64 word counts differ, on a "
+                   f"stratified subset of {m} of the 2^30 counters (one uniform pick per stratum "
+                   "of 16); ulp32 = FP32 ulp at the FP64 value. Near zero the FP32 value differs "
+                   "from the FP64 one by up to X_i 2^-23 because U keeps its top 23 bits, hence "
+                   "large ulp ratios there")
     return res
 
 
