@@ -52,6 +52,9 @@ def parse_args():
     p.add_argument("--batch-requests", type=int, default=None,
                    help="time only zig_batch on the first K requests of the serving mix "
                         "(a small case for profiling) and print its line")
+    p.add_argument("--clock-soak", type=float, default=1.0,
+                   help="seconds of untimed launches run under the clock sampler just before "
+                        "the timed region (0 for profiling commands)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the CPU baseline, e2e, variant and batch measurements")
     return p.parse_args()
@@ -156,17 +159,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-CLOCK_SOAK_S = 1.0  # the sampler's window before the timed region
-
-
-def soak(step, first: int, ms_per_step: float, stream):
-    """Untimed steps for about CLOCK_SOAK_S seconds, run just before the
-    timed region with the clock sampler already running, so that it sees
-    the same launches under load even when K steps last only milliseconds.
-    Returns the number of steps run (their counters follow `first`)."""
+def soak(step, first: int, ms_per_step: float, stream, seconds: float):
+    """Untimed steps for about `seconds`, run just before the timed region
+    with the clock sampler already running, so that it sees the same
+    launches under load even when K steps last only milliseconds.  Returns
+    the number of steps run (their counters follow `first`)."""
     import torch
 
-    count = max(1, int(CLOCK_SOAK_S * 1e3 / max(ms_per_step, 1e-3)))
+    count = int(seconds * 1e3 / max(ms_per_step, 1e-3)) if seconds > 0 else 0
     for k in range(count):
         step(first + k)
     torch.cuda.synchronize()
@@ -259,7 +259,7 @@ def run_fused(args):
     torch.cuda.synchronize()
     est_ms = e0.elapsed_time(e1) / max(1, args.warmup)
     with ClockSampler(local_rank) as clk:
-        nsoak = soak(step, args.warmup, est_ms, stream)
+        nsoak = soak(step, args.warmup, est_ms, stream, args.clock_soak)
         first = args.warmup + nsoak
         if world > 1:
             dist.barrier()
@@ -301,7 +301,7 @@ def run_fused(args):
                    "keying": args.keying, "l2": "nothing is stored; no flush needed",
                    "parallelism": f"counter-range shards x{world}"},
         "clocks": dict(clk.summary(), window=f"{nsoak} untimed steps of the same launch "
-                       f"(~{CLOCK_SOAK_S:.0f} s) just before the timed region, and the region"),
+                       f"(~{args.clock_soak:g} s) just before the timed region, and the region"),
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": None,
@@ -361,7 +361,7 @@ def run_zig(args):
     torch.cuda.synchronize()
     est_ms = e0.elapsed_time(e1) / max(1, args.warmup)
     with ClockSampler(local_rank) as clk:
-        nsoak = soak(step, args.warmup, est_ms, stream)
+        nsoak = soak(step, args.warmup, est_ms, stream, args.clock_soak)
         first = args.warmup + nsoak
         if world > 1:
             dist.barrier()
@@ -395,7 +395,7 @@ def run_zig(args):
                        n * esize / 2**30, ">" if n * esize > 129e6 else "<="),
                    "parallelism": f"counter-range shards x{world}"},
         "clocks": dict(clk.summary(), window=f"{nsoak} untimed steps of the same launch "
-                       f"(~{CLOCK_SOAK_S:.0f} s) just before the timed region, and the region"),
+                       f"(~{args.clock_soak:g} s) just before the timed region, and the region"),
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,

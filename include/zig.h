@@ -208,9 +208,10 @@ zig_status zig_normal(void* out, uint64_t n, uint64_t seed, uint64_t offset,
  *   d_sums[k] = sum of x^(k+1), k = 0..3, accumulated per thread in the
  *     variates' precision over one tile of a thread's values (32 at the
  *     default FP32 shape, 64 with packed keying) or directly (FP64) and
- *     then in FP64; the draws finished by the fringe stages are added in
- *     their completion order, so the sums are reproducible to about 1e-15
- *     relative, not bit for bit;
+ *     then in FP64; every thread adds its values in a fixed order (the
+ *     fringe stages' draws when a warp finishes them), each thread block
+ *     sums its threads in thread order and the last block the blocks in
+ *     block order, so a call repeats bit for bit on the same device;
  *   d_hist[b], b < 4098: count of variates with floor(256 x) + 2048 = b for
  *     -8 <= x < 8, b = 4096 for x < -8, b = 4097 for x >= 8 or NaN (exact).
  * d_workspace: caller-owned device scratch of at least

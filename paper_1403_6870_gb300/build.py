@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "libzig.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["zig_gen.cu"]
-CU_HEADERS = ["zig_device.cuh", "zig_batch.cuh"]
+CU_HEADERS = ["zig_device.cuh", "zig_batch.cuh", "zig_emul.h"]
 CPP_SOURCES = ["zig_tables.cpp", "zig_tune.cpp"]
 
 

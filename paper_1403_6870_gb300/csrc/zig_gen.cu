@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "zig_device.cuh"
+#include "zig_emul.h"
 #include "zig_internal.h"
 
 namespace zig {
@@ -75,7 +76,7 @@ struct VecStore<float, 8> {
 #define ZIG_GEN_V64 4
 #endif
 #ifndef ZIG_GEN_R64
-#define ZIG_GEN_R64 4
+#define ZIG_GEN_R64 8
 #endif
 #ifndef ZIG_GEN_V32
 #define ZIG_GEN_V32 8
@@ -97,10 +98,12 @@ constexpr unsigned kWaitBit = 1u << 9;       // status bit: a bounded wait gave 
 // the CTAs per SM the register budget is compiled for.  The outputs do not
 // depend on the shape: element t is always the variate of counter
 // offset + t.
-template <int V_, int R_, int MB_, int U_ = 0>
+template <int V_, int R_, int MB_, int U_ = 0, int E_ = 0>
 struct Shape {
-  // U: vectors whose Philox chains are interleaved (0: the precision's default)
-  static constexpr int V = V_, R = R_, MB = MB_, U = U_;
+  // U: vectors whose Philox chains are interleaved (0: the precision's default);
+  // E: FP64 outputs per vector whose step-2 product is formed from integers
+  // (zig_emul.h) instead of on the FP64 pipe (packed keying only)
+  static constexpr int V = V_, R = R_, MB = MB_, U = U_, E = E_;
 };
 
 // Default shapes (the batch and fused kernels use these).
@@ -120,8 +123,19 @@ struct GenShape<float> : Shape<ZIG_GEN_V32, ZIG_GEN_R32, ZIG_GEN_MINBLOCKS> {};
 #endif
 template <typename T>
 struct PackedShape;
+// Integer-formed products per FP64 vector (0: none).  Measured on GB300 at
+// 2^28 packed FP64 normals: 433 Gsamples/s with 0, 339 with 1, 272 with 2
+// of 4 (the kernel is not bound by the FP64 pipe alone, and each integer
+// product is a long dependent chain), so it is off; kept as a build option.
+#ifndef ZIG_PACKED_EM64
+#define ZIG_PACKED_EM64 0
+#endif
+#ifndef ZIG_PACKED_R64
+#define ZIG_PACKED_R64 4
+#endif
 template <>
-struct PackedShape<double> : Shape<ZIG_GEN_V64, ZIG_GEN_R64, ZIG_GEN_MINBLOCKS> {};
+struct PackedShape<double>
+    : Shape<ZIG_GEN_V64, ZIG_PACKED_R64, ZIG_GEN_MINBLOCKS, 0, ZIG_PACKED_EM64> {};
 #ifndef ZIG_PACKED_MB32
 #define ZIG_PACKED_MB32 2
 #endif
@@ -569,6 +583,21 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
   return fm;
 }
 
+// Step 2 as fast_value, with the product RN(U sX) formed from integers
+// (zig_emul.h): the same bits, without the FP64 pipe.  Placeholders of
+// fringe draws (sX = 0) come out as arbitrary bits and are overwritten.
+template <int DIST, int IB = 8, typename T>
+__device__ __forceinline__ T fast_value_int(uint32_t lo, uint32_t hi, const T* sX) {
+  if constexpr (sizeof(T) == 4) {
+    return fast_value<DIST, IB>(lo, hi, sX);
+  } else {
+    constexpr uint32_t kMask = ((DIST == ZIG_NORMAL ? 2u : 1u) << IB) - 1u;
+    const uint64_t m = ((uint64_t)(hi >> 12) << 32) | __funnelshift_r(lo, hi, 12);
+    return __longlong_as_double(
+        (long long)emul_u_times_x(m, (uint64_t)__double_as_longlong(sX[lo & kMask])));
+  }
+}
+
 // Packed keying (KEY 1) for one thread's tile: each Philox block
 // gives B = V / P whole outputs (P = 2 FP64 words or 4 FP32 lanes), so a
 // vector takes V / P blocks.  MODE 0: the vector's counters start at a
@@ -597,8 +626,10 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
         const uint32_t d = (uint32_t)(r * kPThreads * B + b);
         const uint4 w = MODE == 0 ? run.block(d, rk) : philox_block(h0 + d, 0u, rk);
         if (sizeof(T) == 8) {
-          v[2 * b] = fast_value<DIST, IB>(w.x, w.y, sX);
-          v[2 * b + 1] = fast_value<DIST, IB>(w.z, w.w, sX);
+          v[2 * b] = 2 * b >= V - Shp::E ? fast_value_int<DIST, IB>(w.x, w.y, sX)
+                                         : fast_value<DIST, IB>(w.x, w.y, sX);
+          v[2 * b + 1] = 2 * b + 1 >= V - Shp::E ? fast_value_int<DIST, IB>(w.z, w.w, sX)
+                                                 : fast_value<DIST, IB>(w.z, w.w, sX);
           f |= ((unsigned)((w.x & kIM) >= L) | ((unsigned)((w.z & kIM) >= L) << 1)) << (2 * b);
         } else {
           v[4 * b] = fast_value<DIST, IB>(w.x, w.x, sX);
@@ -991,8 +1022,8 @@ template <typename T>
 struct Variants;
 template <>
 struct Variants<double> {
-  static constexpr int V[kVariants] = {GenShape<double>::V, 4, 2, 4, 4};
-  static constexpr int R[kVariants] = {GenShape<double>::R, 2, 4, 4, 4};
+  static constexpr int V[kVariants] = {GenShape<double>::V, 4, 4, 4, 4};
+  static constexpr int R[kVariants] = {GenShape<double>::R, 4, 16, 8, 8};
   static constexpr int MB[kVariants] = {GenShape<double>::MB, 3, 3, 4, 2};
 };
 template <>

@@ -106,7 +106,7 @@ def test_tune_candidates(zig):
     assert len(f64) == 5 and len(f32) == 5
     # the defaults come first; all shapes distinct; outputs per thread and
     # tile fit a warp's ring reservation (32 V R <= 2048)
-    assert (f64[0]["V"], f64[0]["R"], f64[0]["min_blocks"]) == (4, 4, 3)
+    assert (f64[0]["V"], f64[0]["R"], f64[0]["min_blocks"]) == (4, 8, 3)
     assert (f32[0]["V"], f32[0]["R"], f32[0]["min_blocks"]) == (8, 4, 3)
     for c in (f64, f32):
         assert len({(e["V"], e["R"], e["min_blocks"]) for e in c}) == len(c)
