@@ -254,7 +254,7 @@ __device__ __forceinline__ int hist_bin(double x) {
 // x^3, x^4 (FP32 values in FP32 over one tile, then added to a double-FP32
 // accumulator (hi, lo) by an error-free two-sum, which keeps GB300's slow
 // FP64 pipe out of the loop; FP64 values in FP64) and counts the value in
-// the CTA's shared-memory histogram.  Outputs still to be patched are skipped here and
+// the CTA's shared-memory histogram.  Outputs still to be patched are
 // counted when the fringe stages put their final value.
 template <typename T>
 struct MomentSink {
@@ -266,6 +266,7 @@ struct MomentSink {
   static constexpr bool kAffine = false;
   __device__ __forceinline__ void init(unsigned* h) {
     hist = h;
+    placeholders = 0u;
     for (int k = 0; k < 4; ++k) {
       acc[k] = 0.0;
       part[k] = (T)0;
@@ -284,16 +285,26 @@ struct MomentSink {
     add_powers(x);
     atomicAdd(&hist[hist_bin(x)], 1u);
   }
-  // Without branches: an output still to be patched adds zero to the power
-  // sums and counts in the unused slot kBins.
+  // Step 2's values lie strictly inside (-8, 8) (|x| < X_0), so their bin
+  // needs no range test.  An output still to be patched holds the
+  // placeholder +0 (its table entry is zero): it adds nothing to the power
+  // sums and one count to bin 2048, which `placeholders` takes back at the
+  // end; the fringe stages count its final value.
+  unsigned placeholders;
   template <int V>
   __device__ __forceinline__ void vec(uint64_t, const T* v, unsigned fringe) {
+    placeholders += __popc(fringe);
 #pragma unroll
     for (int k = 0; k < V; ++k) {
-      const bool patch = (fringe >> k) & 1u;
-      add_powers(patch ? (T)0 : v[k]);
-      atomicAdd(&hist[patch ? kBins : hist_bin(v[k])], 1u);
+      add_powers(v[k]);
+      atomicAdd(&hist[inner_bin(v[k])], 1u);
     }
+  }
+  static __device__ __forceinline__ int inner_bin(float x) {
+    return __float2int_rd(__fmul_rn(x, 256.0f)) + 2048;
+  }
+  static __device__ __forceinline__ int inner_bin(double x) {
+    return __double2int_rd(__dmul_rn(x, 256.0)) + 2048;
   }
   __device__ __forceinline__ void tile_end() {
 #pragma unroll
@@ -612,6 +623,7 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
   static_assert(V % P == 0, "a vector holds whole blocks");
   static_assert(V * R <= 64, "at most 64 outputs per thread and tile");
   static_assert(IB == 8 || sizeof(T) == 8, "a 32-bit packed word has room for 8 index bits");
+  static_assert(Shp::E == 0 || !Sink::kReduce, "integer products leave no +0 placeholders");
   constexpr uint32_t kIM = (1u << IB) - 1u;
   FringeMask<V * R> fm = 0;
   const uint64_t h0 = g0 >> SH;
@@ -822,7 +834,9 @@ __global__ void __launch_bounds__(kThreads, Shp::MB)
 
   const int tid = threadIdx.x;
   for (int k = tid; k < (2 << IB); k += kThreads) {
-    const T X = Prec<T>::X(dev_tab<IB>(DIST), k & ((1 << IB) - 1));
+    // entries i >= L_max are zero: step 2 leaves the placeholder +0 there
+    const int i = k & ((1 << IB) - 1);
+    const T X = i < dev_tab<IB>(DIST).L ? Prec<T>::X(dev_tab<IB>(DIST), i) : (T)0;
     sh.sX[k] = (k >> IB) ? -X : X;
   }
   if (Sink::kReduce)
@@ -842,6 +856,7 @@ __global__ void __launch_bounds__(kThreads, Shp::MB)
     double (*rsum)[4] = reinterpret_cast<double (*)[4]>(&sh.wq[0]);
     __shared__ bool last_cta;
     sink.finish();
+    if (sink.placeholders) atomicSub(&shist[2048], sink.placeholders);
     __syncthreads();
     for (int k = 0; k < 4; ++k) rsum[tid][k] = sink.acc[k];
     __syncthreads();
