@@ -33,6 +33,7 @@ DEFAULT_WORKLOAD = "normal_f64_2p28"
 KERNEL_SRCS = [os.path.join(ROOT, "paper_1403_6870_gb300", "csrc", f)
                for f in ("zig_gen.cu", "zig_device.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gen_kernel_normal_f64_traffic.txt")
+PIPES_FILE = os.path.join(ROOT, "profiles", "gen_kernel_moments_f32_pipes.txt")
 
 
 def parse_args():
@@ -102,6 +103,31 @@ def recorded_traffic(n: int):
         if int(kv["n_captured"]) != n:
             return None
         return float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])
+    except Exception:
+        return None
+
+
+def recorded_pipes(keying: str):
+    """ncu pipe utilisation of the fused-reduction kernel (FP32 normals) for
+    a keying ("index" or "packed") from the committed summary, or None if
+    the kernel source changed since it was taken.  Lines `<keying>.<key>:
+    value` hold the busy percentages of the integer multiply pipe
+    (fmaheavy), the ALU pipe and instruction issue."""
+    try:
+        kv = {}
+        with open(PIPES_FILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        pipes = {name: float(kv[f"{keying}.{name}_pct"]) for name in ("fmaheavy", "alu", "issue")}
+        bound = max(pipes, key=pipes.get)
+        return {"bound": "alu", "pipe": bound, "achieved": pipes[bound], "peak": 100.0,
+                "unit": "% busy (ncu, of the pipe's peak)", "frac": pipes[bound] / 100.0,
+                "pipes_pct": pipes, "traffic": None,
+                "source": os.path.relpath(PIPES_FILE, ROOT) + f" (n = {kv['n_captured']})"}
     except Exception:
         return None
 
@@ -303,12 +329,13 @@ def run_fused(args):
         "clocks": dict(clk.summary(), window=f"{nsoak} untimed steps of the same launch "
                        f"(~{args.clock_soak:g} s) just before the timed region, and the region"),
         "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_source": f"SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz",
-                     "kernel": "gen_kernel<normal,float,MomentSink>",
-                     "algorithmic_ops_per_launch": n * (0.25 if keying else 1.0)
-                     * PHILOX_OPS_PER_BLOCK},
+        "roofline": dict(recorded_pipes(args.keying) or {
+            "bound": "alu", "achieved": None, "peak": 100.0, "frac": None, "traffic": None,
+            "unit": "% busy (ncu)", "note": "no ncu summary for the current kernel source"},
+            kernel="gen_kernel<normal,float,MomentSink>",
+            philox={"achieved_tops": achieved, "lane_issue_peak_tops": peak,
+                    "peak_source": f"SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz",
+                    "ops_per_launch": n * (0.25 if keying else 1.0) * PHILOX_OPS_PER_BLOCK}),
         "e2e": {"value": n * e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * 8 + 4098 * 8},
         "device_status": z.zig_strerror(z.zig_status_poll(stream)),
@@ -561,11 +588,13 @@ def measure_fused(z, stream, reps: int = 5):
         rate = n / (ms / 1e3)
         achieved = rate * blocks * PHILOX_OPS_PER_BLOCK / 1e12
         res[name] = {"gsamples_s": rate / 1e9, "ms_per_launch": ms,
-                     "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                                  "unit": "Tops/s", "frac": achieved / peak}}
-    res["note"] = (f"2^34 FP32 normals reduced to 4 power sums and a 4098-bin histogram; "
-                   f"alu peak = SMs x 4 x 32 lanes x {mhz:.0f} MHz; achieved counts "
-                   f"{PHILOX_OPS_PER_BLOCK} Philox operations per block")
+                     "roofline": recorded_pipes("packed" if keying else "index"),
+                     "philox_tops": achieved, "lane_issue_peak_tops": peak}
+    res["note"] = ("2^34 FP32 normals reduced to 4 power sums and a 4098-bin histogram; "
+                   "roofline: the busiest of the integer multiply pipe, the ALU pipe and "
+                   "instruction issue in the committed ncu summary of the same kernel source "
+                   f"(null if stale); philox_tops counts {PHILOX_OPS_PER_BLOCK} operations per "
+                   f"Philox block against SMs x 4 x 32 lanes x {mhz:.0f} MHz")
     return res
 
 

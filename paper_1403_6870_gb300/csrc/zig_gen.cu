@@ -6,10 +6,12 @@
 // shared-memory lookup of X_i, one fused multiply-add and a vector store.
 //
 // Every warp runs steps 1-2 for its outputs: a draw whose layer index is
-// not below L_max is stored like the others (a placeholder) and its
-// position is appended to the warp's queue in shared memory.  Whenever the
-// queue holds 32 positions the warp runs the rest of the algorithm for
-// them in stages, so the 32 lanes execute the same step:
+// not below L_max is stored like the others (a placeholder) and marked in
+// its lane's mask for the tile; a lane with any such draw appends one entry
+// (its first position and the mask) to the warp's queue in shared memory.
+// Whenever the queue holds 32 entries the warp runs the rest of the
+// algorithm in stages, one marked draw per entry and lane, so the 32 lanes
+// execute the same step:
 //   stage 1: steps 3-7 (alias pick, first attempt in the overhang box);
 //   stage 2: one more attempt for each rejected draw (step 8 keeps j);
 //   stage 3: tail draws, through the complete sampler of zig_device.cuh.
@@ -205,7 +207,10 @@ __device__ __forceinline__ RoundKeys device_keys(uint64_t seed) {
 struct WarpQueues {
   uint64_t q[kQueue];
   uint64_t rp[kQueue], rs[kQueue], rw[kQueue], tq[kQueue];
-  int nq, nr, nt;
+  // fringe masks: a lane's first output position in a tile (mp) and the
+  // mask of its outputs there whose layer index is not below L_max (mm)
+  uint64_t mp[kQueue], mm[kQueue];
+  int nq, nr, nt, nm;
 };
 
 // Shared state of one CTA (X_i of an index of IB bits).
@@ -689,21 +694,44 @@ struct ReduceOut {
   unsigned* ticket;               // workspace: CTAs finished (zero before launch)
 };
 
-// Fringe work of one warp: stage 1 on its queued positions, 32 at a time,
-// while 32 or more are queued (all of them when draining), with the retry
-// and tail stages run whenever 32 or more entries wait (all when draining).
-// The sink travels by value so that the caller keeps its copy in registers.
+// Fringe work of one warp.  Stage 1 runs on the queued fringe masks, 32
+// entries at a time while 32 or more are queued (all of them when
+// draining): each lane takes the lowest set bit of its entry (output s of
+// the lane's tile, at position base + (s / V) kPThreads V + s % V) and
+// queues the rest of the entry again.  Whole-sampler items (head and tail
+// elements) run when draining.  The retry and tail stages run whenever 32
+// or more entries wait (all when draining).  The sink travels by value so
+// that the caller keeps its copy in registers.
 #ifndef ZIG_FRINGE_ATTR
 #define ZIG_FRINGE_ATTR __forceinline__
 #endif
-template <int DIST, typename T, int KEY, int IB, typename Sink>
+template <int DIST, typename T, int KEY, int IB, int V, typename Sink>
 __device__ ZIG_FRINGE_ATTR Sink fringe_work(Sink sink, WarpQueues& wq, uint64_t seed,
                                             uint64_t offset, Limits lim, bool drain) {
   const int lane = threadIdx.x & 31;
   const RoundKeys rk = device_keys(seed);
   SideCounts c{wq.nr, wq.nt};
-  int nq = wq.nq;
+  int nq = wq.nq, nm = wq.nm;
   __syncwarp();  // every lane's placeholder stores come before the fixes
+  while (nm >= 32 || (drain && nm > 0)) {
+    const int take = nm < 32 ? nm : 32;
+    const bool active = lane < take;
+    const uint64_t base = active ? wq.mp[nm - take + lane] : 0;
+    const uint64_t mask = active ? wq.mm[nm - take + lane] : 0;
+    nm -= take;
+    __syncwarp();  // entries read before their slots are refilled
+    const uint64_t rest = mask & (mask - 1u);
+    const int k = claim(rest != 0u, nm);
+    if (rest != 0u) {
+      wq.mp[k] = base;
+      wq.mm[k] = rest;
+    }
+    const int sb = active ? __ffsll((long long)mask) - 1 : 0;
+    const uint64_t item = base + (uint64_t)((sb / V) * (kPThreads * V) + sb % V);
+    stage_new<DIST, T, ~kWholeTag, KEY, IB>(sink, offset, rk, lim, active, item, wq, c);
+    __syncwarp();
+    side_stages<DIST, T, KEY, IB>(sink, seed, offset, rk, lim, 32, wq, c);
+  }
   while (nq >= 32 || (drain && nq > 0)) {
     const int take = nq < 32 ? nq : 32;
     const bool active = lane < take;
@@ -718,6 +746,7 @@ __device__ ZIG_FRINGE_ATTR Sink fringe_work(Sink sink, WarpQueues& wq, uint64_t 
   __syncwarp();
   if (lane == 0) {
     wq.nq = nq;
+    wq.nm = nm;
     wq.nr = c.retry;
     wq.nt = c.tail;
   }
@@ -767,6 +796,7 @@ __device__ __forceinline__ void gen_tiles(State& sh, Sink& sink, const T* sX, ui
       wq.nq = total;
       wq.nr = 0;
       wq.nt = 0;
+      wq.nm = 0;
     }
     __syncwarp();
   }
@@ -792,33 +822,25 @@ __device__ __forceinline__ void gen_tiles(State& sh, Sink& sink, const T* sX, ui
       else
         fm = producer_tile_packed<DIST, T, Shp, 1, IB>(sink, g0, v0, nvec, full, rk, sX, L);
     }
-    // queue the positions; run the fringe stages whenever 32 are queued
-    FringeMask<V * R> m = fm;
-    while (__any_sync(0xFFFFFFFFu, m != 0)) {
-      const int cnt = mask_popc(m);
-      int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
+    // queue this lane's fringe mask as one entry; run the fringe stages
+    // whenever 32 entries are queued (fewer than 32 are queued here)
+    const bool has = fm != 0;
+    const unsigned b = __ballot_sync(0xFFFFFFFFu, has);
+    if (b != 0u) {
+      const int nm = wq.nm;
+      if (has) {
+        const int k = nm + __popc(b & ((1u << lane) - 1u));
+        wq.mp[k] = p0;
+        wq.mm[k] = (uint64_t)fm;
       }
-      const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-      const int nq = wq.nq;  // < 32 here
-      int slot = nq + incl - cnt;
-      while (m != 0 && slot < kQueue) {
-        const int s = mask_ffs(m) - 1;
-        m &= m - 1u;
-        wq.q[slot++] = p0 + (uint64_t)((s / V) * (kPThreads * V) + (s % V));
-      }
+      const int total = nm + __popc(b);
       __syncwarp();
-      const int added = total < kQueue - nq ? total : kQueue - nq;
-      if (lane == 0) wq.nq = nq + added;
+      if (lane == 0) wq.nm = total;
       __syncwarp();
-      if (nq + added >= 32)
-        sink = fringe_work<DIST, T, KEY, IB>(sink, wq, seed, offset, lim, false);
+      if (total >= 32) sink = fringe_work<DIST, T, KEY, IB, V>(sink, wq, seed, offset, lim, false);
     }
   }
-  sink = fringe_work<DIST, T, KEY, IB>(sink, wq, seed, offset, lim, true);
+  sink = fringe_work<DIST, T, KEY, IB, V>(sink, wq, seed, offset, lim, true);
 }
 
 // One launch covers outputs [0, n) (layout as in gen_tiles); CTA b takes
