@@ -119,3 +119,32 @@ def test_generate_rejects_unknown_keying(zig):
         zig.zig_generate(W.NORMAL, 2, b, 16, 1, 0)
     with pytest.raises(zig.ZigError):
         zig.zig_generate(7, 0, b, 16, 1, 0)
+
+
+def _zero_fringe():
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden",
+                           "packed_f32_zero_fringe.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("dist", [W.EXP, W.NORMAL])
+@pytest.mark.parametrize("shift", [1000, 1001, 4096])
+def test_packed_f32_fringe_draw_with_zero_u(zig, orc, dist, shift):
+    """A fringe draw whose U is zero: its first overhang attempt starts at
+    u_x = 0 (the box's right edge X_j), and for the normal the sign comes
+    from a first word whose U bits are all zero (counters from
+    tests/golden/packed_f32_zero_fringe.json; the normal's has its sign bit
+    set).  Offsets put it in the vector body at both block alignments."""
+    fx = _zero_fringe()
+    g = fx["exp" if dist == W.EXP else "normal"]
+    n = 8192
+    off = g - shift
+    out, _ = gen(zig, dist, W.F32, n, fx["seed"], off)
+    v, words, margin = ref(orc, dist, W.F32, fx["seed"], off, n)
+    got = out.cpu().numpy()
+    check(got, v, words, margin)
+    assert words[shift] > 1  # the draw left step 2
+    assert zig.zig_status_poll() == zig.ZIG_OK

@@ -35,3 +35,21 @@ def test_percentages(orc):
     # eps: the widest band (chord to curve) as a share of its box height
     assert _printed("widest_band_percent_exponential", 100.0 * t.eps)
     assert _printed("rejection_tests_eliminated_percent_exponential", 100.0 * (1.0 - t.eps))
+
+
+def test_packed_zero_fringe_fixture(orc):
+    """tests/golden/packed_f32_zero_fringe.json (written by
+    make_packed_zero.py from the oracle's Philox): each counter's packed
+    FP32 first word has a layer index >= L_max and U = 0; the normal's has
+    its sign bit set."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden",
+                           "packed_f32_zero_fringe.json")) as f:
+        fx = json.load(f)
+    for name, dist in (("exp", orc.EXP), ("normal", orc.NORMAL)):
+        w = orc.packed_words(fx["seed"], fx[name], orc.F32, 1)[0]
+        assert (w & 0xFF) >= orc.tables(dist).L and (w >> 41) == 0
+        if name == "normal":
+            assert (w >> 8) & 1 == 1
