@@ -633,6 +633,11 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
   FringeMask<V * R> fm = 0;
   const uint64_t h0 = g0 >> SH;
   const RunState run(h0, rk);
+  // FP32: a block's four index bytes are compared at once (byte b of add
+  // is 256 - L, L >= 128: a byte's low seven bits plus it carry into its
+  // top bit exactly when the byte is at least L); the mask layout is the
+  // one packed_flag_offset decodes
+  const uint32_t add = (256u - L) * 0x01010101u;
 #pragma unroll kPackedUnrollR
   for (int r = 0; r < R; ++r) {
     T v[V];
@@ -653,9 +658,9 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
           v[4 * b + 1] = fast_value<DIST, IB>(w.y, w.y, sX);
           v[4 * b + 2] = fast_value<DIST, IB>(w.z, w.z, sX);
           v[4 * b + 3] = fast_value<DIST, IB>(w.w, w.w, sX);
-          f |= ((unsigned)((w.x & kIM) >= L) | ((unsigned)((w.y & kIM) >= L) << 1) |
-                ((unsigned)((w.z & kIM) >= L) << 2) | ((unsigned)((w.w & kIM) >= L) << 3))
-               << (4 * b);
+          const uint32_t t = __byte_perm(__byte_perm(w.x, w.y, 0x0040u),
+                                         __byte_perm(w.z, w.w, 0x0040u), 0x5410u);
+          f |= ((((t & 0x7F7F7F7Fu) + add) & t) & 0x80808080u) >> b;
         }
       }
     } else {
@@ -664,17 +669,39 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
         const uint64_t g = g0 + (uint64_t)(r * kPThreads * V + k);
         const uint64_t w = packed_word_of<T>(philox_block(g >> SH, 0u, rk), g);
         v[k] = fast_value<DIST, IB>((uint32_t)w, (uint32_t)(w >> 32), sX);
-        f |= (unsigned)(((uint32_t)w & kIM) >= L) << k;
+        const unsigned flag = (unsigned)(((uint32_t)w & kIM) >= L);
+        f |= sizeof(T) == 8 ? flag << k : flag << (8 * (k % 4) + 7 - k / 4);
       }
     }
     const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
     if (full || vi < nvec) {
       sink.template vec<V>(vi, v, f);
-      fm |= (FringeMask<V * R>)f << (r * V);
+      if (sizeof(T) == 8) {
+        fm |= (FringeMask<V * R>)f << (r * V);
+      } else {
+        // block r B + b of the tile: word (r B + b) / 8, shifted right by
+        // (r B + b) % 8 (B = V / 4 blocks per vector)
+        const int j = (r * B) % 8;
+        fm |= (FringeMask<V * R>)(f >> j) << (32 * ((r * B) / 8));
+      }
     }
   }
   sink.tile_end();
   return fm;
+}
+
+// Offset within a lane's tile of the output marked by bit sb of its fringe
+// mask: FP64 and per-index keying, output sb (vector sb / V, element
+// sb % V); packed FP32, the byte layout of producer_tile_packed (output q
+// of block bb at bit 32 (bb / 8) + 8 q + 7 - bb % 8, block bb = vector
+// bb / B, outputs 4 (bb % B) + q, B = V / 4).
+template <int V, bool BYTES>
+__device__ __forceinline__ uint32_t fringe_offset(int sb) {
+  if (!BYTES) return (uint32_t)((sb / V) * (kPThreads * V) + sb % V);
+  constexpr int B = V / 4;
+  const int within = sb & 31;
+  const int bb = 8 * (sb >> 5) + 7 - (within & 7);
+  return (uint32_t)((bb / B) * (kPThreads * V) + 4 * (bb % B) + (within >> 3));
 }
 
 // Scratch of zig_moments_noalloc: the same layout as a caller workspace
@@ -727,7 +754,7 @@ __device__ ZIG_FRINGE_ATTR Sink fringe_work(Sink sink, WarpQueues& wq, uint64_t 
       wq.mm[k] = rest;
     }
     const int sb = active ? __ffsll((long long)mask) - 1 : 0;
-    const uint64_t item = base + (uint64_t)((sb / V) * (kPThreads * V) + sb % V);
+    const uint64_t item = base + fringe_offset<V, KEY == 1 && sizeof(T) == 4>(sb);
     stage_new<DIST, T, ~kWholeTag, KEY, IB>(sink, offset, rk, lim, active, item, wq, c);
     __syncwarp();
     side_stages<DIST, T, KEY, IB>(sink, seed, offset, rk, lim, 32, wq, c);
