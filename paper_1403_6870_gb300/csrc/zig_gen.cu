@@ -557,6 +557,32 @@ __device__ __forceinline__ int mask_ffs(unsigned long long m) { return __ffsll(m
 #endif
 constexpr int kPackedUnrollR = ZIG_PACKED_UNROLL_R;
 
+// Fringe flags.  With 8 index bits the flags of four outputs come from one
+// byte-wise compare: index_flags gathers the four words' index bytes (byte
+// permutes) and, with each byte of add equal to 256 - L (L >= 128), sets
+// bit 8 q + 7 exactly when output q's byte is at least L (the byte's low
+// seven bits plus 256 - L carry into its top bit when it is >= L, and
+// never out of the byte).  Group b of a vector shifts its flags right by
+// b; place_flags puts vector r's flags of group bb = r V / 4 + b at bit
+// 32 (bb / 8) + 8 q + 7 - bb % 8 of the tile mask (fringe_offset decodes
+// it).  Otherwise (10 index bits, packed FP64) output s of the tile is
+// bit s (vector s / V, element s % V).
+template <typename T, int V, int IB, int KEY>
+__host__ __device__ constexpr bool byte_flags() {
+  return IB == 8 && V % 4 == 0 && (KEY == 0 || sizeof(T) == 4);
+}
+__device__ __forceinline__ uint32_t index_flags(const uint32_t* lo, uint32_t add) {
+  const uint32_t t =
+      __byte_perm(__byte_perm(lo[0], lo[1], 0x0040u), __byte_perm(lo[2], lo[3], 0x0040u), 0x5410u);
+  return (((t & 0x7F7F7F7Fu) + add) & t) & 0x80808080u;
+}
+template <int V, int R, bool BYTES>
+__device__ __forceinline__ FringeMask<V * R> place_flags(unsigned f, int r) {
+  if (!BYTES) return (FringeMask<V * R>)f << (r * V);
+  constexpr int B = V / 4;
+  return (FringeMask<V * R>)(f >> ((r * B) % 8)) << (32 * ((r * B) / 8));
+}
+
 // Steps 1-2 for one thread's S = V R outputs of a tile: vector r
 // holds counters g0 + r kPThreads V + [0, V) and is vector v0 + r kPThreads
 // of the output.  The Philox chains of U vectors are interleaved (U from
@@ -573,11 +599,14 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
   constexpr int kUnrollR =
       Shp::U > 0 ? Shp::U : (sizeof(T) == 8 ? ZIG_GEN_UNROLL_R64 : ZIG_GEN_UNROLL_R32);
   static_assert(V * R <= 64, "at most 64 outputs per thread and tile");
+  constexpr bool kBytes = byte_flags<T, V, IB, 0>();
+  const uint32_t add = (256u - L) * 0x01010101u;
   FringeMask<V * R> fm = 0;
   const RunState run(g0, rk);
 #pragma unroll kUnrollR
   for (int r = 0; r < R; ++r) {
     T v[V];
+    uint32_t lo[V];
     unsigned f = 0;
 #pragma unroll
     for (int k = 0; k < V; ++k) {
@@ -587,12 +616,17 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile(
         v[k] = affine_value<DIST>(w.x, w.y, sink.sB, sink.sD);
       else
         v[k] = fast_value<DIST, IB>(w.x, w.y, sX);
-      f |= (unsigned)((w.x & ((1u << IB) - 1u)) >= L) << k;
+      lo[k] = w.x;
+      if (!kBytes) f |= (unsigned)((w.x & ((1u << IB) - 1u)) >= L) << k;
+    }
+    if (kBytes) {
+#pragma unroll
+      for (int b = 0; b < V / 4; ++b) f |= index_flags(lo + 4 * b, add) >> b;
     }
     const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
     if (full || vi < nvec) {
       sink.template vec<V>(vi, v, f);
-      fm |= (FringeMask<V * R>)f << (r * V);
+      fm |= place_flags<V, R, kBytes>(f, r);
     }
   }
   sink.tile_end();
@@ -633,11 +667,7 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
   FringeMask<V * R> fm = 0;
   const uint64_t h0 = g0 >> SH;
   const RunState run(h0, rk);
-  // FP32: a block's four index bytes are compared at once (byte b of add
-  // is 256 - L, L >= 128: a byte's low seven bits plus it carry into its
-  // top bit exactly when the byte is at least L); the mask layout is the
-  // one packed_flag_offset decodes
-  const uint32_t add = (256u - L) * 0x01010101u;
+  const uint32_t add = (256u - L) * 0x01010101u;  // FP32: index_flags
 #pragma unroll kPackedUnrollR
   for (int r = 0; r < R; ++r) {
     T v[V];
@@ -658,9 +688,8 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
           v[4 * b + 1] = fast_value<DIST, IB>(w.y, w.y, sX);
           v[4 * b + 2] = fast_value<DIST, IB>(w.z, w.z, sX);
           v[4 * b + 3] = fast_value<DIST, IB>(w.w, w.w, sX);
-          const uint32_t t = __byte_perm(__byte_perm(w.x, w.y, 0x0040u),
-                                         __byte_perm(w.z, w.w, 0x0040u), 0x5410u);
-          f |= ((((t & 0x7F7F7F7Fu) + add) & t) & 0x80808080u) >> b;
+          const uint32_t lo[4] = {w.x, w.y, w.z, w.w};
+          f |= index_flags(lo, add) >> b;
         }
       }
     } else {
@@ -676,14 +705,7 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
     const uint64_t vi = v0 + (uint64_t)(r * kPThreads);
     if (full || vi < nvec) {
       sink.template vec<V>(vi, v, f);
-      if (sizeof(T) == 8) {
-        fm |= (FringeMask<V * R>)f << (r * V);
-      } else {
-        // block r B + b of the tile: word (r B + b) / 8, shifted right by
-        // (r B + b) % 8 (B = V / 4 blocks per vector)
-        const int j = (r * B) % 8;
-        fm |= (FringeMask<V * R>)(f >> j) << (32 * ((r * B) / 8));
-      }
+      fm |= place_flags<V, R, byte_flags<T, V, IB, 1>()>(f, r);
     }
   }
   sink.tile_end();
@@ -691,10 +713,7 @@ __device__ __forceinline__ FringeMask<Shp::V * Shp::R> producer_tile_packed(
 }
 
 // Offset within a lane's tile of the output marked by bit sb of its fringe
-// mask: FP64 and per-index keying, output sb (vector sb / V, element
-// sb % V); packed FP32, the byte layout of producer_tile_packed (output q
-// of block bb at bit 32 (bb / 8) + 8 q + 7 - bb % 8, block bb = vector
-// bb / B, outputs 4 (bb % B) + q, B = V / 4).
+// mask (layouts of place_flags).
 template <int V, bool BYTES>
 __device__ __forceinline__ uint32_t fringe_offset(int sb) {
   if (!BYTES) return (uint32_t)((sb / V) * (kPThreads * V) + sb % V);
@@ -703,7 +722,6 @@ __device__ __forceinline__ uint32_t fringe_offset(int sb) {
   const int bb = 8 * (sb >> 5) + 7 - (within & 7);
   return (uint32_t)((bb / B) * (kPThreads * V) + 4 * (bb % B) + (within >> 3));
 }
-
 // Scratch of zig_moments_noalloc: the same layout as a caller workspace
 // (a 256-byte ticket area, then 4 FP64 partials per CTA), in static device
 // memory that every device loading the library holds until exit.  Host
@@ -754,7 +772,7 @@ __device__ ZIG_FRINGE_ATTR Sink fringe_work(Sink sink, WarpQueues& wq, uint64_t 
       wq.mm[k] = rest;
     }
     const int sb = active ? __ffsll((long long)mask) - 1 : 0;
-    const uint64_t item = base + fringe_offset<V, KEY == 1 && sizeof(T) == 4>(sb);
+    const uint64_t item = base + fringe_offset<V, byte_flags<T, V, IB, KEY>()>(sb);
     stage_new<DIST, T, ~kWholeTag, KEY, IB>(sink, offset, rk, lim, active, item, wq, c);
     __syncwarp();
     side_stages<DIST, T, KEY, IB>(sink, seed, offset, rk, lim, 32, wq, c);
