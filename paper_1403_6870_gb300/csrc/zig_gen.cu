@@ -173,14 +173,14 @@ struct RunState {
   __device__ __forceinline__ uint4 block(uint32_t d, const RoundKeys& rk) const {
     const uint64_t p = base + (uint64_t)kM0 * d;
     const uint32_t n2 = (uint32_t)(p >> 32) ^ rk.k1[0], n3 = (uint32_t)p;
-    const uint64_t p1 = (uint64_t)kM1 * n2;  // round 2
+    const uint64_t p1 = mul_wide(kM1, n2);  // round 2
     return philox_rounds3to10((uint32_t)(p1 >> 32) ^ rk.k0[1], (uint32_t)p1, uhi ^ n3, ulo, rk);
   }
   // first word of block 0 for counter g0 + d (no wrap of the low word)
   __device__ __forceinline__ uint2 word(uint32_t d, const RoundKeys& rk) const {
     const uint64_t p = base + (uint64_t)kM0 * d;
     const uint32_t n2 = (uint32_t)(p >> 32) ^ rk.k1[0], n3 = (uint32_t)p;
-    const uint64_t p1 = (uint64_t)kM1 * n2;  // round 2
+    const uint64_t p1 = mul_wide(kM1, n2);  // round 2
     return philox_rounds3to10_first((uint32_t)(p1 >> 32) ^ rk.k0[1], (uint32_t)p1, uhi ^ n3,
                                     ulo, rk);
   }
