@@ -7,7 +7,9 @@ be within the rounding bound of its accumulation scheme (FP32 partials of
 at most m terms, m = 32 at the default FP32 shape and 64 with packed
 keying, then summed in double-FP32 by an error-free two-sum, whose error is
 far below the bound):
-|S_gpu - S| <= (m + 4) 2^-24 sum |x|^k (FP32) or 1e-12 sum |x|^k (FP64).
+|S_gpu - S| <= (m + 4) 2^-24 sum |x|^k (FP32) or 1e-12 sum |x|^k (FP64);
+FP32 sums are also held to the error actually achieved, within one unit of
+2^-24 sum |x|^k (measured: at most 0.17).
 Packed keying (zig_moments_keyed) is checked against the oracle's packed
 word source the same way.
 At the full 2^34 size: moments within 5 standard errors of the closed
@@ -65,6 +67,12 @@ def test_moments_match_oracle(zig, orc, dist, dtype, keying):
         assert int(hist.sum()) == n
         tol = _tol(dtype, keying, abss)
         assert np.all(np.abs(sums - ref) <= tol), (sums, ref, tol)
+        if dtype == 0:
+            # the achieved error (fixed inputs, so the sums repeat bit for
+            # bit) is far inside the worst case: measured on GB300 at most
+            # 0.17 units of 2^-24 sum |x|^k at 2^22 and 2^26 values; one
+            # unit flags a systematic accumulation error
+            assert np.all(np.abs(sums - ref) <= 2.0**-24 * abss), (sums, ref, abss)
 
 
 def test_moments_small_and_edge_sizes(zig, orc):
