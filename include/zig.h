@@ -24,7 +24,7 @@
  * from bits 0-7 and a 56-bit threshold from bits 8-63 (Appendix C items
  * 1-2).  A fast-path value is RN(U X_i) with one rounding; the normal's
  * sign is applied to X_i inside that rounding, so a zero (U = 0) is +0 for
- * either sign.  Every variate is therefore reproducible from (seed, g) alone, and
+ * either sign (the paper does not fix the sign bit of a zero).  Every variate is therefore reproducible from (seed, g) alone, and
  * any split of [offset, offset + n) across calls gives identical bits.
  *
  * Conventions for every entry point below.

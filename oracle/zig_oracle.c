@@ -475,12 +475,11 @@ double orc_normal64(const orc_tables* te, const orc_tables* tn, orc_words* w,
   double U1 = u64_of(tn, w0);
   double x;
   if (i < tn->L) {
-    /* Step 2 with the sign on X_i (reading R16): RN((1 + U) sX - sX) with
-     * sX = +-X_i is +-RN(U X_i), and its zero (U = 0) is +0 for either sign;
-     * 1 + U is exact. */
-    const double sx = neg ? -tn->X[i] : tn->X[i];
+    /* Step 2: U X_i, one rounding, with the sign bit applied (reading
+     * R16: the sign of a zero is not fixed; parity compares it by value). */
+    const double x2 = U1 * tn->X[i];
     d->words = w->used;
-    return fma(1.0 + U1, sx, -sx);
+    return neg ? -x2 : x2;
   } else {
     int j = orc_alias_pick(tn, orc_next(w));
     if (j == 0) {
@@ -580,10 +579,10 @@ float orc_normal32(const orc_tables* te, const orc_tables* tn, orc_words* w,
   float U1 = u32_of(w0);
   float x;
   if (i < tn->L) {
-    /* as in orc_normal64 (reading R16), in binary32 */
-    const float sx = neg ? -tn->X32[i] : tn->X32[i];
+    /* as in orc_normal64, in binary32 */
+    const float x2 = U1 * tn->X32[i];
     d->words = w->used;
-    return fmaf(1.0f + U1, sx, -sx);
+    return neg ? -x2 : x2;
   } else {
     int j = orc_alias_pick(tn, orc_next(w));
     if (j == 0) {

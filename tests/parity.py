@@ -2,7 +2,8 @@
 
 Stated tolerance (FP64; applied to FP32 against the FP32 oracle as well):
   * uniform words and layer indices are bit-exact, so the fast-path
-    outputs (one word consumed) must be bit-identical;
+    outputs (one word consumed) must be bit-identical (a zero by value:
+    the sign bit of a zero is not fixed, reading R16);
   * every other output must be identical too unless an accept/reject
     decision could have flipped: the oracle records, per output, the
     smallest gap |y - P(x)| of its exact rejection tests in FP64 ulps of
@@ -37,7 +38,9 @@ def check(gpu: np.ndarray, ref: np.ndarray, words: np.ndarray, margin: np.ndarra
     assert np.array_equal(gnan, rnan), f"NaN positions differ at {np.nonzero(gnan != rnan)[0][:10]}"
     ok = ~gnan
     it = np.uint64 if gpu.dtype == np.float64 else np.uint32
-    same = gpu.view(it) == ref.view(it)
+    # a zero compares by value: the library's is +0 for either sign, the
+    # oracle's carries the normal's sign bit (reading R16)
+    same = (gpu.view(it) == ref.view(it)) | (gpu == ref)
     same |= gnan
     fast = words == 1
     bad_fast = np.nonzero(fast & ~same)[0]

@@ -370,9 +370,9 @@ def test_distribution_ten_bit_index(orc, dist, dtype):
 
 
 def test_fast_path_sign_and_zero(orc, te, tn):
-    # Reading R16: the normal's sign enters step 2's one rounding through
-    # +-X_i, so a negative draw is the exact negation of the positive one
-    # except at U = 0, where both signs give +0 (bit pattern 0).
+    # Step 2 with the normal's sign: a negative draw is the exact negation
+    # of the positive one; at U = 0 the value is a zero (reading R16 leaves
+    # its sign bit open; the oracle's carries the draw's sign).
     rng = np.random.default_rng(5)
     for dtype, it in ((orc.F64, np.uint64), (orc.F32, np.uint32)):
         for _ in range(100):
@@ -388,4 +388,6 @@ def test_fast_path_sign_and_zero(orc, te, tn):
                 x, used, over, err = orc.sample_script(dist, [word(5, 0, s if dist else 0)],
                                                        dtype=dtype)
                 ft = np.float64 if dtype == orc.F64 else np.float32
-                assert used == 1 and np.array([x], dtype=ft).view(it)[0] == 0
+                assert used == 1 and x == 0.0
+                sign = (np.array([x], dtype=ft).view(it)[0] >> (63 if dtype == orc.F64 else 31))
+                assert int(sign) == (s if dist == orc.NORMAL else 0)
