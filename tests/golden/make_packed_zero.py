@@ -1,8 +1,9 @@
 """Write packed_f32_zero_fringe.json: for each distribution, a counter whose
 packed-keying FP32 draw leaves step 2 (layer index >= L_max) with U = 0, so
 that a GPU test checks a fringe draw whose first overhang attempt starts
-at u_x = 0 (for the normal, one whose sign bit is set).  Runs find_packed_zero.c against the oracle's
-Philox only (oracle/liborc.so); the search takes a few minutes."""
+at u_x = 0 (for the normal, one whose sign bit is set).  Runs
+find_packed_zero.c against the oracle's Philox only (oracle/liborc.so),
+on all host cores; it finds both counters within seconds."""
 import json
 import os
 import subprocess
