@@ -75,6 +75,18 @@ def test_moments_match_oracle(zig, orc, dist, dtype, keying):
             assert np.all(np.abs(sums - ref) <= 2.0**-24 * abss), (sums, ref, abss)
 
 
+@pytest.mark.parametrize("keying", [0, 1])
+def test_moments_across_the_counter_carry(zig, orc, keying):
+    """Counters crossing 2^32 (the high counter word changes mid-tile):
+    histogram exact, sums within the bound, FP32 normals."""
+    n, seed, off = (1 << 20) + 7, 0x0123456789ABCDEF, 2**32 - 5001
+    sums, hist = _run(zig, 1, 0, n, seed, off, keying)
+    assert zig.zig_status_poll() == zig.ZIG_OK
+    ref, abss, rhist, errs = orc.moments(1, 0, seed, off, n, keying=keying)
+    assert errs == 0 and np.array_equal(hist, rhist)
+    assert np.all(np.abs(sums - ref) <= _tol(0, keying, abss)), (sums, ref)
+
+
 def test_moments_small_and_edge_sizes(zig, orc):
     for n in (1, 7, 1000, 3584 * 7 + 5):
         sums, hist = _run(zig, 1, 0, n, W.SEED, 17)

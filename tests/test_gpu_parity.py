@@ -224,3 +224,25 @@ def test_f32_zeros_are_positive_and_match_oracle(zig, orc):
         ref, words, margin = oracle_ref(orc, dist, W.F32, W.SEED, 12345, idx=idx)
         assert np.all(ref == 0.0) and np.all(words == 1)  # zeros of step 2 there too
     assert zig.zig_status_poll() == zig.ZIG_OK
+
+
+def test_status_word_is_taken_once_from_any_stream(zig):
+    """zig_status_poll reads and clears the device's status word with one
+    atomic exchange ordered on the stream it is given, and synchronises
+    only that stream: a loop-limit condition recorded by work on one
+    stream is reported by a poll on another stream once that work is
+    done, and the next poll finds the word clear."""
+    n = 1 << 20
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    try:
+        zig.zig_set_fringe_limits(1, 16)
+        zig.zig_exponential(out, n, W.SEED, 0, stream=a)
+        a.synchronize()
+        zig.zig_set_fringe_limits(64, 16)
+        assert zig.zig_status_poll(b) == zig.ZIG_E_LOOP_LIMIT
+        assert zig.zig_status_poll(a) == zig.ZIG_OK
+        zig.zig_normal(out, n, W.SEED, n, stream=b)
+        assert zig.zig_status_poll(b) == zig.ZIG_OK
+    finally:
+        zig.zig_set_fringe_limits(64, 16)
