@@ -813,6 +813,9 @@ def measure_batch(z, stream, reps: int = 10):
             fn = z.zig_normal if q["dist"] == W.NORMAL else z.zig_exponential
             fn(b, q["n"], q["seed"], q["offset"], stream=cs)
 
+    # the batch's tiles per claim, tuned on this batch before timing
+    chunk, chunk_table = z.zig_batch_autotune(d_reqs, len(reqs), ws, reps=3,
+                                              stream=torch.cuda.current_stream())
     ms_batch = timed_graph(run_batch)
     lat = done.cpu().numpy().astype(np.float64) / 1e6  # ms from batch start
     ms_plain = timed_graph(run_plain)
@@ -842,6 +845,7 @@ def measure_batch(z, stream, reps: int = 10):
     rate = total / (ms_batch / 1e3) / 1e9
     return {"requests": len(reqs), "variates": total,
             "bytes": int(sum(q["n"] * (8 if q["dtype"] else 4) for q in reqs)),
+            "autotune": {"chosen_chunk_tiles": chunk, "measured": chunk_table},
             "batch_graph": {"ms": ms_batch, "gsamples_s": rate,
                             "p50_ms": float(np.percentile(lat, 50)),
                             "p99_ms": float(np.percentile(lat, 99))},

@@ -335,6 +335,42 @@ zig_status zig_batch(const zig_request* d_reqs, uint32_t count,
                      size_t workspace_bytes, void* stream);
 
 /*
+ * Batch tuning.  The paper has no batched interface and tunes its CPU code
+ * by hand; this is the serving mix's tile scheduling.  The persistent batch
+ * kernel's CTAs claim chunks of consecutive tiles (a tile is the plain
+ * kernel's unit: 256 threads x V x R outputs of one request); the chunk
+ * size changes only the order in which tiles are served, never an output
+ * bit.
+ */
+typedef struct zig_batch_tune_entry {
+  uint32_t chunk; /* tiles per claim */
+  double ms;      /* measured time of one zig_batch call of the tuned batch */
+} zig_batch_tune_entry;
+
+/*
+ * zig_batch_autotune -- time zig_batch on the caller's batch (d_reqs,
+ * count > 0, d_workspace as for zig_batch) with each candidate chunk size
+ * (64, 32, 128, 16 tiles), reps timed calls after one warm-up call each
+ * (1 <= reps <= 100), with CUDA events on stream, and select the fastest
+ * for later zig_batch calls on the current device.  The calls write the
+ * batch's outputs (the same values every time; no completion times).
+ * Writes up to max_results entries of results (nullable), the number of
+ * candidates to *n_results and the choice to *chosen_chunk (both nullable).
+ * Synchronises stream.  Returns ZIG_OK or the errors of zig_batch.
+ */
+zig_status zig_batch_autotune(const zig_request* d_reqs, uint32_t count, void* d_workspace,
+                              size_t workspace_bytes, int reps, void* stream,
+                              zig_batch_tune_entry* results, int max_results, int* n_results,
+                              uint32_t* chosen_chunk);
+
+/* Set the tiles per claim of later zig_batch calls on the current device
+ * (1..4096; default 64).  ZIG_OK, ZIG_E_INVAL or ZIG_E_CUDA. */
+zig_status zig_batch_set_chunk(uint32_t chunk);
+
+/* The tiles per claim zig_batch uses on the current device (0 on error). */
+uint32_t zig_batch_get_chunk(void);
+
+/*
  * zig_status_poll -- read and clear this device's status word.
  * The read-and-clear is one atomic exchange ordered on stream (after the
  * work queued there), and the call then synchronises that stream only, not

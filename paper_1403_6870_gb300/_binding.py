@@ -297,6 +297,40 @@ def zig_batch(d_reqs, count: int, workspace, done_ns=None, stream=None) -> None:
                   workspace.data_ptr(), wbytes, _stream_handle(stream, workspace)), "zig_batch")
 
 
+class zig_batch_tune_entry(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_uint32), ("ms", ctypes.c_double)]
+
+
+_batch_autotune = _sig("zig_batch_autotune", _int,
+                       [_vp, ctypes.c_uint32, _vp, ctypes.c_size_t, _int, _vp,
+                        ctypes.POINTER(zig_batch_tune_entry), _int, ctypes.POINTER(_int),
+                        ctypes.POINTER(ctypes.c_uint32)])
+_batch_set_chunk = _sig("zig_batch_set_chunk", _int, [ctypes.c_uint32])
+_batch_get_chunk = _sig("zig_batch_get_chunk", ctypes.c_uint32, [])
+
+
+def zig_batch_autotune(d_reqs, count: int, workspace, reps: int = 3, stream=None):
+    """Time zig_batch with each candidate chunk size on this batch and keep
+    the fastest; returns (chosen chunk, [{"chunk", "ms"}, ...])."""
+    wbytes = workspace.numel() * workspace.element_size()
+    buf = (zig_batch_tune_entry * 16)()
+    n = _int(0)
+    chosen = ctypes.c_uint32(0)
+    _check(_batch_autotune(d_reqs.data_ptr(), int(count), workspace.data_ptr(), wbytes, int(reps),
+                           _stream_handle(stream, workspace), buf, 16, ctypes.byref(n),
+                           ctypes.byref(chosen)), "zig_batch_autotune")
+    return int(chosen.value), [{"chunk": int(buf[k].chunk), "ms": float(buf[k].ms)}
+                               for k in range(min(n.value, 16))]
+
+
+def zig_batch_set_chunk(chunk: int) -> None:
+    _check(_batch_set_chunk(int(chunk)), "zig_batch_set_chunk")
+
+
+def zig_batch_get_chunk() -> int:
+    return int(_batch_get_chunk())
+
+
 def zig_status_poll(stream=None) -> int:
     """Returns the device status (ZIG_OK or ZIG_E_LOOP_LIMIT) and clears it."""
     st = _status_poll(_stream_handle(stream))
@@ -359,5 +393,6 @@ def raw_call(name: str, *args) -> int:  # noqa: C901
     (used to exercise argument checks without raising)."""
     table = {"zig_exponential": _exponential, "zig_normal": _normal, "zig_moments": _moments,
              "zig_generate": _generate,
-             "zig_set_fringe_limits": _set_limits, "zig_status_poll": _status_poll}
+             "zig_set_fringe_limits": _set_limits, "zig_status_poll": _status_poll,
+             "zig_batch_autotune": _batch_autotune}
     return int(table[name](*args))

@@ -988,6 +988,7 @@ struct DeviceState {
   int sms = 0;
   char name[256] = {0};
   Selection sel[2][2];  // [dist][dtype]
+  std::atomic<uint32_t> batch_chunk{kBatchChunkDefault};  // zig_batch tiles per claim
 };
 DeviceState g_dev[kMaxDevices];
 
@@ -1366,6 +1367,37 @@ zig_status preload_moment_kernels(int dev) {
   return st;
 }
 
+// zig_batch's two launches with `chunk` tiles per claim (arguments checked
+// by the caller).
+zig_status launch_batch(const zig_request* d_reqs, uint32_t count, unsigned long long* d_done_ns,
+                        void* d_workspace, cudaStream_t s, int dev, uint32_t chunk) {
+  BatchHeader* hdr = (BatchHeader*)d_workspace;
+  BatchReq* reqs = (BatchReq*)((char*)d_workspace + batch_header_bytes());
+  const uint32_t nranges = (uint32_t)(g_dev[dev].sms < kBatchMaxRanges ? g_dev[dev].sms
+                                                                       : kBatchMaxRanges);
+  batch_prep_kernel<<<1, 1024, 0, s>>>(d_reqs, count, reqs, hdr, d_done_ns, nranges, chunk);
+  if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
+  const unsigned grid = (unsigned)(g_dev[dev].sms * batch_occupancy(dev));
+  Limits lim{g_max_att.load(), g_max_tail.load()};
+  batch_kernel<<<grid, kThreads, 0, s>>>(reqs, hdr, lim);
+  if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
+  return ZIG_OK;
+}
+
+// Arguments of zig_batch / zig_batch_autotune; the device on success.
+zig_status batch_args(const zig_request* d_reqs, uint32_t count, unsigned long long* d_done_ns,
+                      void* d_workspace, size_t workspace_bytes, int* dev) {
+  if (d_reqs == nullptr || d_workspace == nullptr) return ZIG_E_INVAL;
+  if (count >= (1u << kBatchReqBits)) return ZIG_E_RANGE;
+  if ((uintptr_t)d_workspace % 16 || (uintptr_t)d_reqs % 8 || (uintptr_t)d_done_ns % 8)
+    return ZIG_E_ALIGN;
+  if (workspace_bytes < batch_ws_bytes(count)) return ZIG_E_NOMEM;
+  zig_status st = current_device(dev);
+  if (st != ZIG_OK) return st;
+  if (!g_dev[*dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
+  return ZIG_OK;
+}
+
 }  // namespace
 
 const zig_tables_export* host_tables(int dist) {
@@ -1687,27 +1719,74 @@ zig_status zig_batch_validate(const zig_request* h_reqs, uint32_t count) {
 zig_status zig_batch(const zig_request* d_reqs, uint32_t count, unsigned long long* d_done_ns,
                      void* d_workspace, size_t workspace_bytes, void* stream) {
   if (count == 0) return ZIG_OK;
-  if (d_reqs == nullptr || d_workspace == nullptr) return ZIG_E_INVAL;
-  if (count >= (1u << kBatchReqBits)) return ZIG_E_RANGE;
-  if ((uintptr_t)d_workspace % 16 || (uintptr_t)d_reqs % 8 || (uintptr_t)d_done_ns % 8)
-    return ZIG_E_ALIGN;
-  if (workspace_bytes < batch_ws_bytes(count)) return ZIG_E_NOMEM;
   int dev;
-  zig_status st = current_device(&dev);
+  const zig_status st = batch_args(d_reqs, count, d_done_ns, d_workspace, workspace_bytes, &dev);
   if (st != ZIG_OK) return st;
-  if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
+  return launch_batch(d_reqs, count, d_done_ns, d_workspace, (cudaStream_t)stream, dev,
+                      g_dev[dev].batch_chunk.load(std::memory_order_relaxed));
+}
+
+zig_status zig_batch_autotune(const zig_request* d_reqs, uint32_t count, void* d_workspace,
+                              size_t workspace_bytes, int reps, void* stream,
+                              zig_batch_tune_entry* results, int max_results, int* n_results,
+                              uint32_t* chosen_chunk) {
+  if (count == 0 || reps < 1 || reps > 100) return ZIG_E_INVAL;
+  int dev;
+  zig_status st = batch_args(d_reqs, count, nullptr, d_workspace, workspace_bytes, &dev);
+  if (st != ZIG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  BatchHeader* hdr = (BatchHeader*)d_workspace;
-  BatchReq* reqs = (BatchReq*)((char*)d_workspace + batch_header_bytes());
-  const uint32_t nranges = (uint32_t)(g_dev[dev].sms < kBatchMaxRanges ? g_dev[dev].sms
-                                                                       : kBatchMaxRanges);
-  batch_prep_kernel<<<1, 1024, 0, s>>>(d_reqs, count, reqs, hdr, d_done_ns, nranges);
-  if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
-  const unsigned grid = (unsigned)(g_dev[dev].sms * batch_occupancy(dev));
-  Limits lim{g_max_att.load(), g_max_tail.load()};
-  batch_kernel<<<grid, kThreads, 0, s>>>(reqs, hdr, lim);
-  if (cudaGetLastError() != cudaSuccess) return ZIG_E_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return ZIG_E_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ZIG_E_CUDA;
+  }
+  uint32_t best = kBatchChunkDefault;
+  float best_ms = -1.0f;
+  for (int k = 0; k < kBatchChunks && st == ZIG_OK; ++k) {
+    const uint32_t c = kBatchChunkCand[k];
+    st = launch_batch(d_reqs, count, nullptr, d_workspace, s, dev, c);  // warm-up
+    if (st == ZIG_OK && cudaEventRecord(e0, s) != cudaSuccess) st = ZIG_E_CUDA;
+    for (int i = 0; i < reps && st == ZIG_OK; ++i)
+      st = launch_batch(d_reqs, count, nullptr, d_workspace, s, dev, c);
+    float ms = 0.0f;
+    if (st == ZIG_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                         cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      st = ZIG_E_CUDA;
+    if (st != ZIG_OK) break;
+    ms /= (float)reps;
+    if (results && k < max_results) results[k] = zig_batch_tune_entry{c, (double)ms};
+    if (best_ms < 0.0f || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ZIG_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  g_dev[dev].batch_chunk.store(best);
+  if (chosen_chunk) *chosen_chunk = best;
+  if (n_results) *n_results = kBatchChunks;
   return ZIG_OK;
+}
+
+zig_status zig_batch_set_chunk(uint32_t chunk) {
+  if (chunk < 1 || chunk > 4096) return ZIG_E_INVAL;
+  int dev;
+  const zig_status st = current_device(&dev);
+  if (st != ZIG_OK) return st;
+  g_dev[dev].batch_chunk.store(chunk);
+  return ZIG_OK;
+}
+
+uint32_t zig_batch_get_chunk(void) {
+  int dev;
+  if (current_device(&dev) != ZIG_OK) return 0;
+  return g_dev[dev].batch_chunk.load();
 }
 
 zig_status zig_status_poll(void* stream) {

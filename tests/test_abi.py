@@ -219,3 +219,16 @@ def test_batch_validate_rules(zig):
         assert status(p1=bad) == Z.ZIG_E_INVAL          # normal standard deviation
     assert status(p0=float("nan")) == Z.ZIG_E_INVAL     # normal mean
     assert Z.zig_batch_validate(np.zeros(0, dtype=Z.request_dtype())) == Z.ZIG_OK
+
+
+def test_batch_tuning_argument_rules(zig):
+    # host-side checks, before any device work
+    for bad in (0, 4097):
+        with pytest.raises(zig.ZigError) as e:
+            zig.zig_batch_set_chunk(bad)
+        assert e.value.status == zig.ZIG_E_INVAL
+    # an empty batch or a rep count out of range
+    assert zig.raw_call("zig_batch_autotune", None, 0, None, 0, 3, None, None, 0, None,
+                        None) == zig.ZIG_E_INVAL
+    assert zig.raw_call("zig_batch_autotune", 0x1000, 4, 0x1000, 1 << 20, 0, None, None, 0,
+                        None, None) == zig.ZIG_E_INVAL

@@ -179,3 +179,45 @@ def test_graph_captured_batch_replays(zig, orc):
                 continue
             assert st > 0
             _compare(orc, q, host[pad:pad + q["n"]], np.arange(q["n"], dtype=np.uint64))
+
+
+def test_batch_autotune_keeps_every_bit(zig):
+    """zig_batch_autotune times the candidate chunk sizes on the caller's
+    batch and keeps the fastest; the chunk size changes only the order in
+    which tiles are served, so the outputs with the tuned chunk, with the
+    smallest candidate and with the default are identical bit for bit."""
+    rng = np.random.default_rng(77)
+    reqs = []
+    for k, n in enumerate([3584 * 40 + 3, 1, 70001, 250000, 5, 3584 * 17]):
+        dist, dtype = k % 2, (k // 2) % 2
+        reqs.append(dict(n=n, dist=dist, dtype=dtype, seed=W.splitmix64(500 + k),
+                         offset=int(rng.integers(0, 2**40)),
+                         p0=float(10 ** rng.uniform(-1, 1)) if dist == 0 else float(rng.uniform(-5, 5)),
+                         p1=0.0 if dist == 0 else float(10 ** rng.uniform(-2, 2))))
+    bufs = _alloc(reqs, lambda r: r % 3)
+    d = torch.from_numpy(zig.pack_requests(reqs).view(np.uint8)).cuda()
+    ws = torch.empty(zig.zig_batch_workspace_bytes(len(reqs)), dtype=torch.uint8, device="cuda")
+
+    def outputs():
+        return [b.cpu().numpy().view(np.uint64 if q["dtype"] else np.uint32).copy()
+                for q, (b, _) in zip(reqs, bufs)]
+
+    try:
+        assert zig.zig_batch_get_chunk() == 64
+        zig.zig_batch(d, len(reqs), ws)
+        ref = outputs()
+        chosen, table = zig.zig_batch_autotune(d, len(reqs), ws, reps=2)
+        assert sorted(e["chunk"] for e in table) == [16, 32, 64, 128]
+        assert all(e["ms"] > 0 for e in table)
+        assert chosen == min(table, key=lambda e: e["ms"])["chunk"]
+        assert zig.zig_batch_get_chunk() == chosen
+        for c in (chosen, 16, 1, 4096):
+            zig.zig_batch_set_chunk(c)
+            for b, _ in bufs:
+                b.fill_(float("nan"))
+            zig.zig_batch(d, len(reqs), ws)
+            got = outputs()
+            assert all(np.array_equal(a, r) for a, r in zip(got, ref)), c
+        assert zig.zig_status_poll() == zig.ZIG_OK
+    finally:
+        zig.zig_batch_set_chunk(64)
