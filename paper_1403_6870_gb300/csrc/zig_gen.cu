@@ -87,10 +87,7 @@ struct VecStore<float, 8> {
 #define ZIG_GEN_R32 4
 #endif
 
-#ifndef ZIG_THREADS
-#define ZIG_THREADS 256
-#endif
-constexpr int kThreads = ZIG_THREADS;  // threads per CTA (8 warps)
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPThreads = kThreads;          // threads making outputs per CTA (all)
 constexpr int kQueue = 64;                   // fringe queue slots per warp
