@@ -805,10 +805,11 @@ __device__ ZIG_FRINGE_ATTR Sink fringe_work(Sink sink, WarpQueues& wq, uint64_t 
 // [t kTile, (t + 1) kTile); thread pt makes vectors t kTile + r kPThreads +
 // pt, r < R.  This CTA takes tiles tile, tile + step, ... below tile_end;
 // if `ends`, its warp 0 also queues the head and tail elements for the
-// whole sampler.  Each warp queues the positions of its draws whose layer
-// index is not below L_max, runs the fringe stages for every 32 of them and
-// drains its queues before returning; on return every output of the CTA's
-// tiles has its final value (the warps have not synchronised).
+// whole sampler.  Each lane queues one entry per tile for its draws whose
+// layer index is not below L_max (its first position and their mask); the
+// warp runs the fringe stages for every 32 entries and drains its queues
+// before returning; on return every output of the CTA's tiles has its final
+// value (the warps have not synchronised).
 template <int DIST, typename T, typename Shp, int KEY, int IB, typename Sink, typename State>
 __device__ __forceinline__ void gen_tiles(State& sh, Sink& sink, const T* sX, uint64_t n,
                                           uint64_t head, uint64_t nvec, uint64_t seed,
