@@ -221,3 +221,24 @@ def test_batch_autotune_keeps_every_bit(zig):
         assert zig.zig_status_poll() == zig.ZIG_OK
     finally:
         zig.zig_batch_set_chunk(64)
+
+
+def test_batch_tile_boundaries(zig, orc):
+    """Requests of 8191, 8192, 8193 and 2 x 8192 + 1 variates (the batch's
+    tile is 8192 outputs for both precisions), each against the oracle's
+    plain map element by element."""
+    rng = np.random.default_rng(31)
+    reqs = []
+    for k, n in enumerate([8191, 8192, 8193, 16385] * 2):
+        dist, dtype = k % 2, k // 4
+        reqs.append(dict(n=n, dist=dist, dtype=dtype, seed=W.splitmix64(900 + k),
+                         offset=int(rng.integers(0, 2**40)),
+                         p0=float(10 ** rng.uniform(-1, 1)) if dist == 0 else float(rng.uniform(-5, 5)),
+                         p1=0.0 if dist == 0 else float(10 ** rng.uniform(-2, 2))))
+    bufs = _alloc(reqs, lambda r: (r * 5) % 4)
+    done = _serve(zig, reqs)
+    for q, (b, pad), d in zip(reqs, bufs, done):
+        host = b.cpu().numpy()
+        assert d > 0
+        assert np.all(np.isnan(host[:pad])) and np.all(np.isnan(host[pad + q["n"]:]))
+        _compare(orc, q, host[pad:pad + q["n"]], np.arange(q["n"], dtype=np.uint64))

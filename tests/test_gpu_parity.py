@@ -246,3 +246,20 @@ def test_status_word_is_taken_once_from_any_stream(zig):
         assert zig.zig_status_poll(b) == zig.ZIG_OK
     finally:
         zig.zig_set_fringe_limits(64, 16)
+
+
+@pytest.mark.parametrize("dist", [W.EXP, W.NORMAL])
+@pytest.mark.parametrize("dtype", [W.F64, W.F32])
+def test_tile_and_wave_boundaries(zig, orc, dist, dtype):
+    """Sizes at the default shapes' tile boundary (256 threads x 32 outputs
+    = 8192 per CTA tile for FP64 V4 R8 and FP32 V8 R4) and at one full wave
+    of the persistent grid (152 SMs x 3 CTAs x 8192) plus a ragged rest,
+    element by element against the oracle."""
+    for n, off in ((8191, 3), (8192, 0), (8193, 2**32 - 4096), (456 * 8192 + 5, 77)):
+        out, buf = gpu_gen(zig, dist, dtype, n, W.SEED, off, pad=1)
+        got = out.cpu().numpy()
+        ref, words, margin = oracle_ref(orc, dist, dtype, W.SEED, off, n=n)
+        check(got, ref, words, margin)
+        tail = buf[1 + n:].cpu().numpy()
+        assert np.all(np.isnan(tail))  # nothing written past the end
+    assert zig.zig_status_poll() == zig.ZIG_OK
