@@ -348,13 +348,16 @@ __device__ __forceinline__ float approx_u(typename Prec<T>::UInt m) {
 
 // Exact rejection test y < exp(-a), decided first in FP32: xa, ya below are
 // FP32 approximations of x and y (from the top 24 bits of U and the binary32
-// tables) whose combined error, with that of expf, stays below 2^-17
-// relative in exp(-a) for every box of both distributions (x <= X_0).  With
-// a margin of 2^-14 the FP32 answer, when it is given, is the one the FP64
-// test y < exp(-a) would give, so the decision is always that of the FP64
-// test; only points within the margin (a fraction of about 1e-4 of the
-// attempts) evaluate the FP64 exp.
-constexpr float kPreTestMargin = 1.0f / 16384.0f;
+// tables) whose combined error, with that of expf (2 ulp), is at most
+// 3.0e-6 (< 2^-18) relative in y / exp(-a) for every box of both
+// distributions at either table width, by an a-priori bound on each step.
+// With a margin of 2^-17 the FP32 answer, when it is given, is the one the
+// FP64 test y < exp(-a) would give, so the decision is always that of the
+// FP64 test; only points within the margin (about 7e-4 of the normal's
+// attempts, 5e-4 of the exponential's) evaluate the FP64 exp.  Each such
+// point costs its warp a double-precision exp on the FP64 pipe, which the
+// fast path also needs.
+constexpr float kPreTestMargin = 1.0f / 131072.0f;
 
 // One attempt inside overhang box j >= 1 at integer uniforms (mx, my)
 // (Table 1 steps 6-7).  Exponential: points above the chord are reflected
