@@ -705,6 +705,10 @@ def measure_precision(z, stream, m: int = 1 << 26):
         ulp = np.ldexp(1.0, np.frexp(r64)[1] - 24)
         ratio = np.where(agree, d / ulp, 0.0)
         ge1 = agree & (np.abs(r64) >= 1.0)
+        # a zero compares by value: the device's normal zero is +0 whatever
+        # the draw's sign (the sign goes inside the one rounding)
+        differ = g32.view(np.uint32) != r32.view(np.uint32)
+        zero_sign = differ & (g32 == 0) & (r32 == 0)
         res[name] = {
             "n": n, "device_full_range": {
                 "max_abs_diff": max_abs, "max_ulp32_where_abs_ge_1": max_ulp_ge1,
@@ -717,8 +721,8 @@ def measure_precision(z, stream, m: int = 1 << 26):
                 "flipped_decisions": flips, "flipped_decision_rate": flips / idx.size,
                 "max_ulp32_vs_fp64_agreeing_paths": float(ratio.max()),
                 "max_ulp32_vs_fp64_where_abs_ge_1": float(ratio[ge1].max()) if ge1.any() else 0.0,
-                "device_fp32_not_equal_oracle_fp32": int(
-                    (g32.view(np.uint32) != r32.view(np.uint32)).sum()),
+                "device_fp32_not_equal_oracle_fp32": int((differ & ~zero_sign).sum()),
+                "zeros_differing_in_sign_only": int(zero_sign.sum()),
                 "oracle_loop_cap_hits": e32 + e64}}
     torch.cuda.empty_cache()
     res["note"] = (f"flipped_decision_rate: the oracle's FP32 and FP64 word counts differ, on a "
