@@ -275,6 +275,15 @@ struct Prec<double> {
     return __hiloint2double((int)(0x3FF00000u | (uint32_t)(m >> 32)), (int)(uint32_t)m);
   }
   static __device__ __forceinline__ double val(UInt m) { return __dsub_rn(one_plus(m), 1.0); }
+  // The same U = m 2^-52 (m <= 2^52, exact) from integer operations: the
+  // leading one of m moved to bit 52 and the exponent added beneath it,
+  // which keeps the subtraction off the FP64 pipe.
+  static __device__ __forceinline__ double val_int(UInt m) {
+    const int lz = __clzll((long long)m);
+    const unsigned long long bits =
+        (m << ((lz - 11) & 63)) + ((unsigned long long)(1033 - lz) << 52);
+    return m == 0 ? 0.0 : __longlong_as_double((long long)bits);
+  }
   static __device__ __forceinline__ double fmat(double a, double b, double c) {
     return __fma_rn(a, b, c);
   }
@@ -309,6 +318,7 @@ struct Prec<float> {
     return __int_as_float((int)(0x3F800000u | m));
   }
   static __device__ __forceinline__ float val(UInt m) { return __fsub_rn(one_plus(m), 1.0f); }
+  static __device__ __forceinline__ float val_int(UInt m) { return val(m); }
   static __device__ __forceinline__ float fmat(float a, float b, float c) {
     return __fmaf_rn(a, b, c);
   }
@@ -370,8 +380,11 @@ constexpr float kPreTestMargin = 1.0f / 131072.0f;
 // the per-box eps of Appendix D item 2 for the exponential, and for the
 // normal the chord test on either side, which sorts the convex boxes
 // (x > 1) and the concave ones (x < 1).  They carry a rounding margin, so
-// the answer is the exact test's.
-template <int DIST, typename T, class Tab>
+// the answer is the exact test's.  kIntU forms U from integers (val_int)
+// instead of with an FP64 subtraction; the packed-keying stages use it
+// (their kernel is bound by the FP64 pipe), the per-index ones do not (there
+// it measured 1 % slower through register allocation).
+template <int DIST, typename T, class Tab, bool kIntU = false>
 __device__ __forceinline__ bool overhang_attempt(const Tab& t, int j,
                                                  typename Prec<T>::UInt mx,
                                                  typename Prec<T>::UInt my, T& x) {
@@ -386,7 +399,7 @@ __device__ __forceinline__ bool overhang_attempt(const Tab& t, int j,
   {
     const typename P::UInt sum = mx + my;
     if (sum < P::acc(t, j)) {
-      x = P::fmat(P::val(mx), P::dX(t, j), P::X(t, j));
+      x = P::fmat((kIntU ? P::val_int(mx) : P::val(mx)), P::dX(t, j), P::X(t, j));
       return true;
     }
     if (DIST != ZIG_EXP && sum > P::rej(t, j)) return false;
@@ -398,12 +411,12 @@ __device__ __forceinline__ bool overhang_attempt(const Tab& t, int j,
   const float aa = DIST == ZIG_EXP ? xa : 0.5f * xa * xa;
   const float e = expf(-aa);
   if (ya > e * (1.0f + kPreTestMargin)) return false;
-  const T xx = P::fmat(P::val(mx), P::dX(t, j), P::X(t, j));
+  const T xx = P::fmat((kIntU ? P::val_int(mx) : P::val(mx)), P::dX(t, j), P::X(t, j));
   if (ya < e * (1.0f - kPreTestMargin)) {
     x = xx;
     return true;
   }
-  const T y = P::fmat(P::val(my), P::df(t, j), P::f(t, j - 1));
+  const T y = P::fmat((kIntU ? P::val_int(my) : P::val(my)), P::df(t, j), P::f(t, j - 1));
   const double xd = (double)xx;
   const double a = DIST == ZIG_EXP ? xd : __dmul_rn(__dmul_rn(xd, xd), 0.5);
   if ((double)y < exp(-a)) {

@@ -340,9 +340,16 @@ struct MomentSink {
   }
 };
 
+// -x by its sign bit: an integer operation, where a negated double would
+// take an instruction on the FP64 pipe (the fast path's busiest unit)
+__device__ __forceinline__ double flip_sign(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+__device__ __forceinline__ float flip_sign(float x) { return -x; }
+
 template <int DIST, typename T, typename Sink>
 __device__ __forceinline__ void put_signed(Sink& sink, uint64_t p, T x, bool negative) {
-  sink.put(p, (DIST == ZIG_NORMAL && negative) ? -x : x);
+  sink.put(p, (DIST == ZIG_NORMAL && negative) ? flip_sign(x) : x);
 }
 
 // A retry's state word: overhang j in bits 0-10 (j < 1024 at either index
@@ -424,7 +431,7 @@ __device__ __forceinline__ void stage_new(Sink& sink, uint64_t offset, const Rou
     if (KEY == 0) b1 = philox_block(g, 1u, rk);
     const uint64_t wy = KEY == 0 ? pack(b1.x, b1.y) : pack(b1.z, b1.w);
     T x;
-    if (overhang_attempt<DIST, T>(t, j, P::ubits(w0), P::ubits(wy), x)) {
+    if (overhang_attempt<DIST, T, DevTabT<IB>, KEY == 1>(t, j, P::ubits(w0), P::ubits(wy), x)) {
       put_signed<DIST, T>(sink, p, x, negative);
     } else if (1 >= lim.max_att) {
       sink.put(p, P::nan());
@@ -482,7 +489,7 @@ __device__ __forceinline__ void stage_retry(Sink& sink, uint64_t offset, const R
     const uint64_t wx = KEY == 0 ? word : pack(b.x, b.y);
     const uint64_t wy = KEY == 0 ? pack(b.x, b.y) : pack(b.z, b.w);
     T x;
-    if (overhang_attempt<DIST, T>(t, j, P::ubits(wx), P::ubits(wy), x)) {
+    if (overhang_attempt<DIST, T, DevTabT<IB>, KEY == 1>(t, j, P::ubits(wx), P::ubits(wy), x)) {
       put_signed<DIST, T>(sink, p, x, negative);
     } else if ((int)(att + 1) >= lim.max_att) {
       sink.put(p, P::nan());
