@@ -77,3 +77,24 @@ def test_ten_bit_packed_fp32_is_rejected(zig):
         zig.zig_generate(W.NORMAL, 1, b, 64, 1, 0, index_bits=10)
     with pytest.raises(zig.ZigError):
         zig.zig_generate(W.NORMAL, 0, b, 64, 1, 0, index_bits=9)
+
+
+@pytest.mark.parametrize("dist,keying", [(W.NORMAL, 0), (W.EXP, 0), (W.NORMAL, 1), (W.EXP, 1)])
+def test_ten_bit_2p28_full_size_sampled(zig, orc, dist, keying):
+    """The launch the bench times for the 1024-slot tables (2^28 FP64
+    outputs in one call, counters from 5 * 2^28): 2^20 sampled positions
+    against the oracle one by one, a few thousand of them fringe draws."""
+    n = 1 << 28
+    offset = 5 * n
+    out, _ = _gen(zig, dist, W.F64, keying, n, W.SEED, offset)
+    assert zig.zig_status_poll() == zig.ZIG_OK
+    idx = W.sample_positions(n, 1 << 20)
+    got = out[torch.from_numpy(idx.astype(np.int64)).cuda()].cpu().numpy()
+    del out
+    torch.cuda.empty_cache()
+    te, tn = orc.tables(0, 10, 52, 54), orc.tables(1, 10, 52, 54)
+    v, errs, words, margin = orc.fill(dist, W.F64, W.SEED, offset, 0, idx=idx, want_words=True,
+                                      want_margin=True, te=te, tn=tn, keying=keying)
+    assert errs == 0
+    rep = check(got, v, words, margin)
+    assert rep["fringe"] > 1000

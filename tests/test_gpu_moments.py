@@ -104,10 +104,13 @@ def test_workspace_too_small(zig):
     assert e.value.status == zig.ZIG_E_NOMEM
 
 
-def test_fused_2p34_normal_f32(zig):
+@pytest.mark.parametrize("keying", [0, 1])
+def test_fused_2p34_normal_f32(zig, keying):
+    # the bench's fused launches (per-index and packed keying): 2^34 values,
+    # their moments and histogram against the normal law
     c = W.WORKLOADS["normal_f32_fused_2p34"]
     n = c["n"]
-    sums, hist = _run(zig, c["dist"], c["dtype"], n, W.SEED, c["offset"])
+    sums, hist = _run(zig, c["dist"], c["dtype"], n, W.SEED, c["offset"], keying=keying)
     assert zig.zig_status_poll() == zig.ZIG_OK
     assert int(hist.sum()) == n
     m = sums / n

@@ -148,3 +148,24 @@ def test_packed_f32_fringe_draw_with_zero_u(zig, orc, dist, shift):
     check(got, v, words, margin)
     assert words[shift] > 1  # the draw left step 2
     assert zig.zig_status_poll() == zig.ZIG_OK
+
+
+@pytest.mark.parametrize("dist,dtype", [(W.NORMAL, W.F64), (W.EXP, W.F64), (W.NORMAL, W.F32),
+                                        (W.EXP, W.F32)])
+def test_packed_2p28_full_size_sampled(zig, orc, dist, dtype):
+    """The launch the bench times for packed keying (2^28 outputs in one
+    call, counters from 5 * 2^28): 2^20 sampled positions against the
+    oracle one by one, about 12 K of them fringe draws."""
+    n = 1 << 28
+    offset = 5 * n
+    out, _ = gen(zig, dist, dtype, n, W.SEED, offset)
+    assert zig.zig_status_poll() == zig.ZIG_OK
+    idx = W.sample_positions(n, 1 << 20)
+    got = out[torch.from_numpy(idx.astype(np.int64)).cuda()].cpu().numpy()
+    del out
+    torch.cuda.empty_cache()
+    v, errs, words, margin = orc.fill(dist, dtype, W.SEED, offset, 0, idx=idx, want_words=True,
+                                      want_margin=True, keying=PACKED)
+    assert errs == 0
+    rep = check(got, v, words, margin)
+    assert rep["fringe"] > 5000
