@@ -375,7 +375,10 @@ uint32_t zig_batch_get_chunk(void);
  * The read-and-clear is one atomic exchange ordered on stream (after the
  * work queued there), and the call then synchronises that stream only, not
  * the device: a bit set meanwhile by work on another stream is kept for
- * the next poll.  Returns ZIG_OK if no device-side condition
+ * the next poll.  Polls may run at the same time from several threads on
+ * several streams (up to 64 in flight at once): each reads its own take,
+ * so a recorded condition is returned by exactly one of them.  Returns
+ * ZIG_OK if no device-side condition
  * was recorded since the last poll, ZIG_E_LOOP_LIMIT if a fringe loop hit
  * its cap (those outputs are NaN), ZIG_E_INVAL if zig_batch skipped an
  * invalid request, ZIG_E_NOTINIT or ZIG_E_CUDA.  ZIG_E_TIMEOUT is

@@ -997,6 +997,7 @@ struct DeviceState {
   char name[256] = {0};
   Selection sel[2][2];  // [dist][dtype]
   std::atomic<uint32_t> batch_chunk{kBatchChunkDefault};  // zig_batch tiles per claim
+  std::atomic<uint32_t> poll_seq{0};  // zig_status_poll's next slot (mod kPollSlots)
 };
 DeviceState g_dev[kMaxDevices];
 
@@ -1161,9 +1162,15 @@ constexpr size_t kTicketBytes = 256;  // workspace: ticket, then the partials
 
 // zig_status_poll's read-and-clear of the status word, ordered on the
 // caller's stream: one atomic exchange, so that a bit set by a kernel on
-// another stream in between is kept for the next poll.
-__device__ unsigned int g_status_taken;
-__global__ void status_take_kernel() { g_status_taken = atomicExch(&g_status, 0u); }
+// another stream in between is kept for the next poll.  Each poll takes
+// into a slot of its own (a ring of kPollSlots per device, handed out on
+// the host), so that polls running at the same time on different streams
+// never read each other's take.
+constexpr unsigned kPollSlots = 64;
+__device__ unsigned int g_status_taken[kPollSlots];
+__global__ void status_take_kernel(unsigned slot) {
+  g_status_taken[slot] = atomicExch(&g_status, 0u);
+}
 
 template <int DIST, typename T, typename Shp = GenShape<T>, int KEY = 0>
 zig_status launch_moments(uint64_t n, uint64_t seed, uint64_t offset, double* d_sums,
@@ -1804,10 +1811,11 @@ zig_status zig_status_poll(void* stream) {
   if (!g_dev[dev].ready.load(std::memory_order_acquire)) return ZIG_E_NOTINIT;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned int h = 0;
-  status_take_kernel<<<1, 1, 0, s>>>();
+  const unsigned slot = g_dev[dev].poll_seq.fetch_add(1u) % kPollSlots;
+  status_take_kernel<<<1, 1, 0, s>>>(slot);
   if (cudaGetLastError() != cudaSuccess ||
-      cudaMemcpyFromSymbolAsync(&h, g_status_taken, sizeof(h), 0, cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess ||
+      cudaMemcpyFromSymbolAsync(&h, g_status_taken, sizeof(h), slot * sizeof(h),
+                                cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return ZIG_E_CUDA;

@@ -248,6 +248,40 @@ def test_status_word_is_taken_once_from_any_stream(zig):
         zig.zig_set_fringe_limits(64, 16)
 
 
+def test_concurrent_polls_report_a_condition_once(zig):
+    """Two threads poll at the same moment, each on its own stream, after a
+    launch recorded a loop-limit condition: exactly one of them reports it
+    and the other finds the word clear, every time (each poll reads the
+    take of its own exchange)."""
+    import threading
+
+    n = 1 << 16
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    gen = torch.cuda.Stream()
+    try:
+        zig.zig_set_fringe_limits(1, 16)
+        for it in range(100):
+            zig.zig_exponential(out, n, W.SEED, it * n, stream=gen)
+            gen.synchronize()
+            got = [None, None]
+            start = threading.Barrier(2)
+
+            def poll(k):
+                start.wait()
+                got[k] = zig.zig_status_poll(streams[k])
+
+            th = [threading.Thread(target=poll, args=(k,)) for k in range(2)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            assert sorted(got) == sorted([zig.ZIG_OK, zig.ZIG_E_LOOP_LIMIT]), (it, got)
+    finally:
+        zig.zig_set_fringe_limits(64, 16)
+        assert zig.zig_status_poll() == zig.ZIG_OK
+
+
 @pytest.mark.parametrize("dist", [W.EXP, W.NORMAL])
 @pytest.mark.parametrize("dtype", [W.F64, W.F32])
 def test_tile_and_wave_boundaries(zig, orc, dist, dtype):
