@@ -45,6 +45,7 @@ struct alignas(16) BatchReq {
 struct BatchHeader {
   uint64_t total_tiles;
   unsigned long long t_start;
+  unsigned long long* done_ns;  // completion times (nullable), this batch's own
   uint32_t count;
   uint32_t nranges;        // tile ranges, one per SM
   unsigned range_counter;  // ranges handed to SMs so far
@@ -67,6 +68,7 @@ constexpr uint32_t kBatchChunkCand[kBatchChunks] = {64, 32, 128, 16};
 constexpr uint32_t kBatchChunkDefault = 64;
 
 __host__ __device__ constexpr size_t batch_header_bytes() { return 256; }
+static_assert(sizeof(BatchHeader) <= 256, "the header fits its slot of the workspace");
 // workspace: header, request states, ranges, SM map
 __host__ __device__ constexpr size_t batch_ranges_offset(uint32_t count) {
   return batch_header_bytes() + (((size_t)count * sizeof(BatchReq) + 255) / 256) * 256;
@@ -129,22 +131,16 @@ struct BatchSink {
   __device__ __forceinline__ void put_mapped(uint64_t p, T y) { out[p] = y; }
 };
 
-struct BatchClock {
-  unsigned long long* done_ns;
-  unsigned long long t_start;
-};
-__device__ BatchClock g_batch_clock;  // set by the prep kernel for the batch
-
 // Subtract `tiles` finished tiles from request r's outstanding count;
-// the CTA that brings it to zero records the completion time.  The caller
-// has made the run's outputs visible (fence) before.
-__device__ __forceinline__ void settle(BatchReq* reqs, uint32_t r, unsigned long long tiles) {
+// the CTA that brings it to zero records the completion time, against the
+// start and into the array that the batch's own header holds (batches on
+// other streams have headers of their own).  The caller has made the run's
+// outputs visible (fence) before.
+__device__ __forceinline__ void settle(const BatchHeader* hdr, BatchReq* reqs, uint32_t r,
+                                       unsigned long long tiles) {
   const unsigned long long old =
       atomicAdd(&reqs[r].remaining, (unsigned long long)(-(long long)tiles));
-  if (old == tiles) {
-    const BatchClock c = g_batch_clock;
-    if (c.done_ns) c.done_ns[r] = globaltimer() - c.t_start;
-  }
+  if (old == tiles && hdr->done_ns) hdr->done_ns[r] = globaltimer() - hdr->t_start;
 }
 
 // Prep: derived request state and the exclusive prefix of tile counts
@@ -235,8 +231,8 @@ __global__ void __launch_bounds__(1024) batch_prep_kernel(const zig_request* __r
   __syncthreads();
   if (tid == 0) {
     const unsigned long long t = globaltimer();
+    hdr->done_ns = done_ns;
     hdr->t_start = t;
-    g_batch_clock = BatchClock{done_ns, t};
   }
 }
 
@@ -391,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, ZIG_BATCH_MINBLOCKS)
     __threadfence();  // this thread's outputs of the session, before it counts
     __syncthreads();
     if (tid == 0) {
-      settle(reqs, q, t1 - t);
+      settle(hdr, reqs, q, t1 - t);
       uint64_t pos = t1, e = end;
       if (pos >= e && !batch_claim(rng, hdr->nranges, home, scan, hdr->chunk, pos, e)) pos = e = 0;
       if (pos < e) {

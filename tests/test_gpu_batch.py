@@ -181,6 +181,53 @@ def test_graph_captured_batch_replays(zig, orc):
             _compare(orc, q, host[pad:pad + q["n"]], np.arange(q["n"], dtype=np.uint64))
 
 
+def test_overlapping_batches_keep_their_own_stamps(zig, orc):
+    """Two batches in flight at once on two streams, each with its own
+    workspace and completion array (a large one and a small one, queued
+    back to back, many times): every request of each batch is stamped in its
+    own array, nothing is written past the small batch's count (its array is
+    padded with sentinels to the large count), and the outputs of both match
+    the oracle."""
+    rng = np.random.default_rng(77)
+
+    def make(count, n_of, seed0):
+        reqs = []
+        for k in range(count):
+            dist, dtype = k % 2, (k // 2) % 2
+            reqs.append(dict(n=n_of(k), dist=dist, dtype=dtype, seed=W.splitmix64(seed0 + k),
+                             offset=int(rng.integers(0, 2**40)),
+                             p0=1.5 if dist == 0 else -0.25, p1=0.0 if dist == 0 else 2.0))
+        return reqs
+
+    big = make(256, lambda k: 20000 + 37 * k, 5000)
+    small = make(4, lambda k: 3000 + k, 9000)
+    bufs_big, bufs_small = _alloc(big, lambda r: 0), _alloc(small, lambda r: 0)
+    d_big = torch.from_numpy(zig.pack_requests(big).view(np.uint8)).cuda()
+    d_small = torch.from_numpy(zig.pack_requests(small).view(np.uint8)).cuda()
+    ws_big = torch.empty(zig.zig_batch_workspace_bytes(len(big)), dtype=torch.uint8, device="cuda")
+    ws_small = torch.empty(zig.zig_batch_workspace_bytes(len(small)), dtype=torch.uint8,
+                           device="cuda")
+    done_big = torch.empty(len(big), dtype=torch.int64, device="cuda")
+    done_small = torch.empty(len(big), dtype=torch.int64, device="cuda")  # padded
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    for it in range(20):
+        done_big.fill_(-1)
+        done_small.fill_(-1)
+        torch.cuda.synchronize()
+        zig.zig_batch(d_big, len(big), ws_big, done_ns=done_big, stream=sa)
+        zig.zig_batch(d_small, len(small), ws_small, done_ns=done_small, stream=sb)
+        torch.cuda.synchronize()
+        assert zig.zig_status_poll() == zig.ZIG_OK
+        db, ds = done_big.cpu().numpy(), done_small.cpu().numpy()
+        assert np.all(db > 0), it
+        assert np.all(ds[:len(small)] > 0), it
+        assert np.all(ds[len(small):] == -1), it
+    for reqs, bufs in ((big[::37], bufs_big[::37]), (small, bufs_small)):
+        for q, (b, pad) in zip(reqs, bufs):
+            host = b.cpu().numpy()
+            _compare(orc, q, host[pad:pad + q["n"]], np.arange(q["n"], dtype=np.uint64))
+
+
 def test_batch_autotune_keeps_every_bit(zig):
     """zig_batch_autotune times the candidate chunk sizes on the caller's
     batch and keeps the fastest; the chunk size changes only the order in
