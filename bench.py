@@ -511,13 +511,17 @@ def cpu_baseline(c):
 
 
 def measure_variants(z, stream, steps: int = 100):
-    """Throughput of the other dist/dtype combinations (2^28 counters each)."""
+    """Throughput of the other dist/dtype combinations (2^28 counters each),
+    and of the FP32 pairs at their workload's own launch size, 2^30."""
     import torch
 
     res = {}
-    n = 1 << 28
-    for name, dist, dtype in (("exp_f64", W.EXP, W.F64), ("normal_f64", W.NORMAL, W.F64),
-                              ("exp_f32", W.EXP, W.F32), ("normal_f32", W.NORMAL, W.F32)):
+    for name, dist, dtype, n in (("exp_f64", W.EXP, W.F64, 1 << 28),
+                                 ("normal_f64", W.NORMAL, W.F64, 1 << 28),
+                                 ("exp_f32", W.EXP, W.F32, 1 << 28),
+                                 ("normal_f32", W.NORMAL, W.F32, 1 << 28),
+                                 ("exp_f32_2p30", W.EXP, W.F32, 1 << 30),
+                                 ("normal_f32_2p30", W.NORMAL, W.F32, 1 << 30)):
         tdt = torch.float64 if dtype == W.F64 else torch.float32
         es = 8 if dtype == W.F64 else 4
         buf = torch.empty(n, dtype=tdt, device="cuda")
@@ -533,7 +537,7 @@ def measure_variants(z, stream, steps: int = 100):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         res[name] = {"gsamples_s": n / (ms / 1e3) / 1e9, "gb_s": n * es / (ms / 1e3) / 1e9,
-                     "ms_per_launch": ms, "launch_shape": chosen}
+                     "ms_per_launch": ms, "n_per_launch": n, "launch_shape": chosen}
         del buf
     return res
 
@@ -735,15 +739,19 @@ def measure_precision(z, stream, m: int = 1 << 26):
 
 def measure_packed(z, stream, steps: int = 100):
     """Packed keying (opt-in, different outputs): the four dist/dtype pairs
-    at 2^28 counters each through zig_generate, with the HBM-write roofline
-    fraction of each against the measured copy peak."""
+    at 2^28 counters each through zig_generate, and the FP32 pairs at their
+    workload's own launch size, 2^30, with the HBM-write roofline fraction
+    of each against the measured copy peak."""
     import torch
 
     peak, _ = measured_peak()
     res = {}
-    n = 1 << 28
-    for name, dist, dtype in (("exp_f64", W.EXP, W.F64), ("normal_f64", W.NORMAL, W.F64),
-                              ("exp_f32", W.EXP, W.F32), ("normal_f32", W.NORMAL, W.F32)):
+    for name, dist, dtype, n in (("exp_f64", W.EXP, W.F64, 1 << 28),
+                                 ("normal_f64", W.NORMAL, W.F64, 1 << 28),
+                                 ("exp_f32", W.EXP, W.F32, 1 << 28),
+                                 ("normal_f32", W.NORMAL, W.F32, 1 << 28),
+                                 ("exp_f32_2p30", W.EXP, W.F32, 1 << 30),
+                                 ("normal_f32_2p30", W.NORMAL, W.F32, 1 << 30)):
         tdt = torch.float64 if dtype == W.F64 else torch.float32
         es = 8 if dtype == W.F64 else 4
         buf = torch.empty(n, dtype=tdt, device="cuda")
@@ -758,7 +766,7 @@ def measure_packed(z, stream, steps: int = 100):
         ms = e0.elapsed_time(e1) / steps
         gbs = n * es / (ms / 1e3) / 1e9
         res[name] = {"gsamples_s": n / (ms / 1e3) / 1e9, "gb_s": gbs, "ms_per_launch": ms,
-                     "roofline_frac": gbs / peak}
+                     "n_per_launch": n, "roofline_frac": gbs / peak}
         del buf
     res["note"] = ("ZIG_KEY_PACKED: one Philox block per 2 FP64 / 4 FP32 fast words; "
                    "outputs differ from per-index keying and are checked against the "
