@@ -310,6 +310,8 @@ def run_fused(args):
     hh = torch.empty(4098, dtype=torch.int64, pin_memory=True)
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = args.steps
+    if world > 1:
+        dist.barrier()
     f0.record(stream)
     for k in range(e2e_steps):
         step(first + args.steps + k)
@@ -318,6 +320,10 @@ def run_fused(args):
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1)
+    if world > 1:  # whole-job rate: the slowest rank's time
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -336,8 +342,8 @@ def run_fused(args):
             philox={"achieved_tops": achieved, "lane_issue_peak_tops": peak,
                     "peak_source": f"SMs x 4 schedulers x 32 lanes x {mhz:.0f} MHz",
                     "ops_per_launch": n * (0.25 if keying else 1.0) * PHILOX_OPS_PER_BLOCK}),
-        "e2e": {"value": n * e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
-                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * 8 + 4098 * 8},
+        "e2e": {"value": n * world * e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": (4 * 8 + 4098 * 8) * world},
         "device_status": z.zig_strerror(z.zig_status_poll(stream)),
     }
     if rank == 0:
@@ -464,9 +470,13 @@ def measure_e2e(z, fn, out, n, esize, counter, stream, args):
     every step: the call writes a page-locked host buffer directly (its
     device alias; NVLink-C2C on Grace), so each step's n outputs cross to
     the host inside the timed region.  For comparison the same steps are
-    also timed writing device memory and copying it to the host buffer."""
+    also timed writing device memory and copying it to the host buffer.
+    With several ranks each region starts after a barrier and its time is
+    the maximum over the ranks, so the values are whole-job rates."""
     import torch
+    import torch.distributed as dist
 
+    _, world, _ = dist_env()
     host = torch.empty(n, dtype=out.dtype, pin_memory=True)
     steps = args.steps  # as many steps as the device-timed region
 
@@ -474,13 +484,20 @@ def measure_e2e(z, fn, out, n, esize, counter, stream, args):
         for k in range(2):
             body(k)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(steps):
             body(2 + k)
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
 
     ms = timed(lambda k: fn(host, n, W.SEED, counter(k), stream=stream))
 
@@ -489,12 +506,13 @@ def measure_e2e(z, fn, out, n, esize, counter, stream, args):
         host.copy_(out, non_blocking=True)
 
     ms_copy = timed(via_copy)
-    return {"value": n * steps / (ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
-            "d2h_bytes_per_step": n * esize, "steps": steps,
-            "d2h_gb_s": n * esize * steps / (ms / 1e3) / 1e9,
+    total = n * world  # outputs of all ranks per step
+    return {"value": total * steps / (ms / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": total * esize, "steps": steps,
+            "d2h_gb_s": total * esize * steps / (ms / 1e3) / 1e9,
             "via_device_buffer_and_copy": {
-                "value": n * steps / (ms_copy / 1e3) / 1e9,
-                "d2h_gb_s": n * esize * steps / (ms_copy / 1e3) / 1e9},
+                "value": total * steps / (ms_copy / 1e3) / 1e9,
+                "d2h_gb_s": total * esize * steps / (ms_copy / 1e3) / 1e9},
             "note": "inputs are (seed, offset, n) launch arguments; each step the call writes "
                     "its n outputs into page-locked host memory (the result is in host memory "
                     "when the step's work ends)"}
