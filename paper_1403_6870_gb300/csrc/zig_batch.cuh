@@ -61,8 +61,8 @@ struct BatchRange {
 constexpr int kBatchMaxRanges = 1024;
 constexpr int kBatchSmSlots = 1024;  // SM id -> range (by %smid)
 // Tiles per claim: the candidates zig_batch_autotune times, and the
-// default (measured on GB300 on the 4096-request mix: 16 tiles 10.60 ms,
-// 32 tiles 10.08 ms, 64 tiles 9.92 ms).
+// default (measured on GB300 on the 4096-request mix: 16 tiles 10.40 ms,
+// 32 tiles 9.95 ms, 128 tiles 9.89 ms, 64 tiles 9.82 ms).
 constexpr int kBatchChunks = 4;
 constexpr uint32_t kBatchChunkCand[kBatchChunks] = {64, 32, 128, 16};
 constexpr uint32_t kBatchChunkDefault = 64;
